@@ -1,0 +1,191 @@
+/*
+ * st.h - C ABI of the GB300 (sm_103a) space-time (p,delta)-Navier-Stokes
+ * slab solver: matrix-free residual and Jacobian action of one DG-in-time
+ * slab, the space-time Vanka smoother, the multigrid V-cycle and the
+ * modified Newton step.
+ *
+ * Discretisation (arXiv 2603.28706):
+ *   - Omega = [0,Lx]x[0,Ly](x[0,Lz]), uniform mesh of nx x ny (x nz) cells;
+ *   - Q2 continuous velocity, Q1 continuous pressure (Taylor-Hood), Sec. 3.1;
+ *   - DG(k) in time, Lagrange basis on the right (k+1)-point Gauss-Radau
+ *     nodes of the slab I_n = (t0, t0+dt], Sec. 3.1, Rem. 3.2;
+ *   - Nitsche boundary terms B_gamma of eq. def-b-gam on Gamma_D, the
+ *     convective boundary term of eq. Defc on all of Gamma; CIP is not part
+ *     of this library.
+ *
+ * Vector layout (all vector arguments): a slab vector is
+ *     U = [V_1 ... V_{k+1} | P_1 ... P_{k+1}]            (eq. slab-system)
+ * V_mu is component-major (component c = 0..dim-1), each component
+ * lexicographic on the Q2 node grid (2nx+1)(2ny+1)(2nz+1), x fastest;
+ * P_mu is lexicographic on the Q1 grid (nx+1)(ny+1)(nz+1).  A velocity field
+ * (v_prev, one time node) is dim*(2nx+1)(2ny+1)(2nz+1) values.  On level l
+ * of the multigrid hierarchy the mesh is n/2^(L-l) cells per direction.
+ *
+ * Ownership: every vector argument is a caller-owned, contiguous DEVICE
+ * pointer, 16-byte aligned, of dtype double (ST_FP64) or float (ST_FP32).
+ * The handle owns all other device memory (coefficient caches, patch
+ * factorisations, coarse operators, Krylov workspace).  Calls are enqueued
+ * on the stream given to st_setup_mesh and return before the GPU finishes,
+ * except st_newton_step and st_mnorm which synchronise that stream (their
+ * results steer host control flow).  Calls on one handle must not overlap.
+ *
+ * Errors: every call returns an st_status.  Invalid arguments give ST_EINVAL
+ * before anything is launched; CUDA failures give ST_ECUDA; st_last_error()
+ * returns a message for the last failure on the handle.  After a status other
+ * than ST_ECUDA the handle stays usable.  No call allocates or frees caller
+ * memory; no call falls back to the CPU.
+ */
+#ifndef ST_H_
+#define ST_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ST_OK = 0,
+  ST_EINVAL = 1,            /* bad argument, size or state                     */
+  ST_ECUDA = 2,             /* a CUDA call or kernel failed                    */
+  ST_ENOMEM = 3,            /* device allocation failed                        */
+  ST_NOT_CONVERGED = 4,     /* Newton or FGMRES missed its tolerance (Sec. 6.2) */
+  ST_LINESEARCH_FAILED = 5, /* Armijo backtracking hit lambda_min (Sec. 6.2)  */
+  ST_SINGULAR_PATCH = 6,    /* a Vanka patch matrix has a zero pivot          */
+  ST_DEVICE_TIMEOUT = 7     /* a bounded device wait ran out                   */
+} st_status;
+
+/* Linearisation of the constitutive term (Sec. 4): Picard eq.
+ * local-tangent-picard, exact Newton eq. local-tangent-exact, modified
+ * Newton (stress-clipped rank one) eq. local-tangent-clip. */
+typedef enum { ST_PIC = 0, ST_EXN = 1, ST_MODN = 2 } st_tangent;
+
+typedef enum { ST_FP64 = 0, ST_FP32 = 1 } st_prec;
+
+/* Problem and solver parameters, copied at setup (plain old data). */
+typedef struct {
+  int dim, nx, ny, nz;        /* dimension 2 or 3; cells per direction (nz ignored in 2D) */
+  double Lx, Ly, Lz;          /* box lengths                                         */
+  int k;                      /* DG degree in time, 0 <= k <= 3 (k+1 Radau nodes)    */
+  double t0, dt;              /* slab I_n = (t0, t0 + dt]                            */
+  double p, delta, nu, nu_inf;/* stress law eq. constitutive-law: 1 < p <= 2, delta > 0 */
+  double sigma_max;           /* modN stress clip (Sec. 4.4); may be +inf             */
+  double gamma1, gamma2;      /* Nitsche penalties, eq. def-b-gam-3                   */
+  unsigned dirichlet_mask;    /* bit s = 2*axis + (upper side): side is Gamma_D      */
+  int inflow_profile;         /* 0: g_D = 0; 1: u_x = vbar*6y(1-y)[*6z(1-z)] scaled,
+                                 lifting constant in x                                */
+  double vbar;                /* inflow mean velocity                                */
+  double q_sign;              /* coefficient of (u.n, q)_{Gamma_D} in B^s; -1 = as
+                                 printed in eq. def-b-gam-2.5                          */
+  int levels;                 /* multigrid levels (1 = no coarsening)                */
+  int pre_smooth, post_smooth;/* Vanka sweeps per level (Sec. 6.3, Sec. 7: 2 + 2)    */
+  double omega;               /* Vanka damping, eq. stmg-vanka-update                */
+  double rho_refresh;         /* patch refresh threshold rho (Sec. 6.3)              */
+  int fgmres_restart, fgmres_maxit, newton_maxit;
+  double tol_abs, tol_rel;    /* Newton stop, eq. nk-stop                            */
+  double lin_rtol;            /* fixed relative FGMRES tolerance (Picard)            */
+  double ew_gamma, ew_alpha, ew_max; /* Eisenstat-Walker forcing, eq. nk-inexact-newton */
+  double armijo_c, lambda_min;/* Armijo backtracking on phi = 1/2 |R|_M^2 (Sec. 6.2) */
+} st_params;
+
+typedef struct {
+  int newton_iters;           /* nonlinear iterations taken                          */
+  int fgmres_iters_total;     /* FGMRES iterations over all Newton steps             */
+  int fgmres_iters_last;
+  int patch_rebuilds;         /* surrogate patch factorisations built                */
+  double lambda_last;         /* last accepted damping                               */
+  double res_norm_initial;    /* |R_n(U^0)|_M                                        */
+  double res_norm_final;      /* |R_n(U^m)|_M at exit                                */
+  int status;                 /* st_status of the solve                              */
+} st_newton_info;
+
+typedef struct st_problem st_problem;
+
+/* Create a problem on the current CUDA device; all work is enqueued on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream).  Validates the
+ * parameters (ST_EINVAL), precomputes the colour classes of cells and the
+ * boundary-face lists of every level, and allocates the handle's caches. */
+st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem** out);
+
+/* Free everything the handle owns.  NULL is accepted. */
+st_status st_destroy(st_problem* h);
+
+/* (k+1)(M_v + M_p) on level `level` (0 = coarsest, levels-1 = finest), the
+ * length of a slab vector (eq. slab-system); 0 for a bad level. */
+size_t st_num_dofs(const st_problem* h, int level);
+
+/* R = R_n(U) = -[(K_t (x) M_x) V - (m_t (x) M_x) v_prev ; 0] + (M_t (x) I) F(U)
+ * (eq. slab-underint), residual convention "right-hand side minus left-hand
+ * side" (eq. disc-residual).  F_mu at node t_n^mu is the spatial residual of
+ * eq. disc with the form A_gamma of eq. def-a-gam (without CIP) and data
+ * B_gamma(g_D) of eq. def-b-gam.  v_prev: left trace u^-(t_{n-1}) (velocity
+ * field); f: body force as Q2 nodal coefficients per time node ((k+1) velocity
+ * fields, layout of V) or NULL.  Finest level.  prec selects the dtype of all
+ * four vectors and the arithmetic. */
+st_status st_residual(st_problem* h, st_prec prec, const void* U, const void* v_prev, const void* f, void* R);
+
+/* Evaluate and keep the state-dependent coefficients of the linearisation at
+ * the iterate U (FP64: A^m = D u^m, Delta^{m,2}, mu^m, eta^m and the rank-one
+ * factor of the tangent at every quadrature point and Radau node, Sec. 4.1;
+ * plus an FP32 copy).  Later st_jacobian_apply calls with U_state == NULL use
+ * them.  Invalidates the preconditioner. */
+st_status st_linearize(st_problem* h, st_tangent tangent, const void* U);
+
+/* out = J_n(U) dU, eq. slab-underint-jac:
+ *   J_n = [[K_t (x) M_x, 0], [0, 0]] + (M_t (x) I) diag(J_1 .. J_{k+1}),
+ * J_mu the spatial linearisation with the selected tangent (Sec. 4.2-4.4,
+ * eq. Jmu-block, eq. Amu-decomp without A_CIP).  U_state != NULL: linearise
+ * at U_state first (as st_linearize); NULL: use the last st_linearize, whose
+ * tangent must equal `tangent` (else ST_EINVAL).  dU and out: slab vectors of
+ * dtype prec; U_state is always double. */
+st_status st_jacobian_apply(st_problem* h, st_tangent tangent, st_prec prec, const void* U_state, const void* dU,
+                            void* out);
+
+/* *out = |r|_M = sqrt(r_v^T M_v r_v + r_p^T M_p r_p) with M_v = M_t (x) M_x and
+ * M_p = M_t (x) M_{x,p} (Sec. 6.1).  r: FP64 slab vector, finest level.
+ * Synchronises the stream. */
+st_status st_mnorm(st_problem* h, const void* r, double* out);
+
+/* Build the Vanka smoother and coarse operators for the current
+ * linearisation: finest-level surrogate patch matrices with the coefficients
+ * frozen at t_rep = midpoint of I_n (eq. surrogate-diag), Galerkin coarse
+ * operators A_l = P^T A_{l+1} P (Sec. 6.3) and their exact cell patches,
+ * batched LU factorisations, the coarsest-level factorisation.  prec: FP32
+ * (mixed) or FP64 storage/arithmetic of the smoother.  Called implicitly by
+ * st_vanka_smooth / st_vcycle when missing. */
+st_status st_precond_setup(st_problem* h, st_prec prec);
+
+/* `sweeps` additive Vanka steps on level `level` (eq. stmg-vanka-update):
+ *   d <- d + omega sum_K R_K^T A_K^{-1} R_K (r - A_l d),
+ * cell patches K with all k+1 time nodes; A_K exact on coarse levels and the
+ * surrogate of eq. surrogate-diag on the finest level.  r, d: slab vectors of
+ * that level, dtype prec; d is updated in place. */
+st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, const void* r, void* d);
+
+/* d = B^{-1} r: one space-time multigrid V-cycle on the finest level
+ * (Sec. 6.3): pre_smooth Vanka sweeps, restriction P^T, recursion, coarsest
+ * solve, prolongation P, post_smooth sweeps.  r, d: finest slab vectors of
+ * dtype prec (d is overwritten). */
+st_status st_vcycle(st_problem* h, st_prec prec, const void* r, void* d);
+
+/* Globalised (modified) Newton on the slab (Sec. 4.1, 6.1-6.3):
+ *   repeat: R = R_n(U); stop if |R|_M <= tol_abs or <= tol_rel |R^0|_M
+ *   (eq. nk-stop); linearise with `tangent`; refresh the preconditioner by the
+ *   rule of Sec. 6.3; solve J dU = R by right-preconditioned FGMRES (FP64) with
+ *   one V-cycle of precision vcycle_prec per iteration to the Eisenstat-Walker
+ *   forcing (eq. nk-inexact-newton; Picard: lin_rtol); Armijo backtracking on
+ *   phi = 1/2 |R|_M^2 (exN, modN; Picard takes lambda = 1); U += lambda dU.
+ * U (FP64 slab vector) is updated in place.  Synchronous.  info may be NULL.
+ * Returns ST_NOT_CONVERGED / ST_LINESEARCH_FAILED when the step fails
+ * (Sec. 6.2: the time-step solve is declared unsuccessful). */
+st_status st_newton_step(st_problem* h, st_tangent tangent, st_prec vcycle_prec, void* U, const void* v_prev,
+                         const void* f, st_newton_info* info);
+
+/* Message describing the last failure on h (never NULL). */
+const char* st_last_error(const st_problem* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H_ */

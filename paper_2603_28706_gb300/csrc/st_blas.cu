@@ -1,0 +1,251 @@
+// Vector kernels (see st_blas.cuh).
+#include <vector>
+
+#include "st_blas.cuh"
+
+namespace st {
+
+namespace {
+
+constexpr int BT = 256;
+constexpr int NPART = 512;  // partial sums of the two-stage reductions
+
+template <typename A, typename B>
+__global__ void cast_kernel(const A* __restrict__ x, B* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (B)x[i];
+}
+
+unsigned grid_for(size_t n) {
+  size_t g = (n + BT - 1) / BT;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// One direction of the global 1D mass operator on a tensor grid of
+// g[0] x g[1] x g[2] points, applied to `nblk` consecutive blocks:
+//   Q2 (order 2): cells [2e, 2e+2], local matrix h * M1 (3x3)
+//   Q1 (order 1): cells [e, e+1], local matrix h * [[1/3, 1/6], [1/6, 1/3]]
+// y_i = scale_b * sum over cells containing i of sum_b M_loc[i - start][b] x[start + b]
+template <typename T, int ORDER>
+__global__ void mass_pass(const T* __restrict__ x, T* __restrict__ y, long g0, long g1, long g2, int dir, double hd,
+                          int nblk, const double* __restrict__ bscale,
+                          int comps_per_node, T m00, T m01, T m02, T m11, T m12, T m22) {
+  const long npt = g0 * g1 * g2;
+  const long total = npt * nblk;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / npt, r = t % npt;
+    const long ix = r % g0, iy = (r / g0) % g1, iz = r / (g0 * g1);
+    const long gd = dir == 0 ? g0 : (dir == 1 ? g1 : g2);
+    const long id = dir == 0 ? ix : (dir == 1 ? iy : iz);
+    const long st = dir == 0 ? 1 : (dir == 1 ? g0 : g0 * g1);
+    const T* xb = x + b * npt + (r - id * st);
+    T acc = 0;
+    // local symmetric matrix entries
+    auto M = [&](int i, int j) -> T {
+      if (ORDER == 2) {
+        const int a = i < j ? i : j, c = i < j ? j : i;
+        if (a == 0) return c == 0 ? m00 : (c == 1 ? m01 : m02);
+        if (a == 1) return c == 1 ? m11 : m12;
+        return m22;
+      } else {
+        return i == j ? m00 : m01;
+      }
+    };
+    const long ncell = (gd - 1) / ORDER;
+    // cells whose node range contains id
+    long e_lo = (id - 1) / ORDER, e_hi = id / ORDER;
+    if (id == 0) e_lo = 0;
+    if (e_hi > ncell - 1) e_hi = ncell - 1;
+    if (e_lo < 0) e_lo = 0;
+    for (long e = e_lo; e <= e_hi; ++e) {
+      const long s0 = e * ORDER;
+      const int a = (int)(id - s0);
+      if (a < 0 || a > ORDER) continue;
+      for (int c = 0; c <= ORDER; ++c) acc += M(a, c) * xb[(s0 + c) * st];
+    }
+    const double sc = bscale ? bscale[b / comps_per_node] : 1.0;
+    y[t] = acc * (T)(hd * sc);
+  }
+}
+
+__global__ void partial_dot(const double* __restrict__ x, const double* __restrict__ y, size_t n,
+                            double* __restrict__ part) {
+  __shared__ double sh[BT];
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) acc += x[i] * y[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = BT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void partial_multidot(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ w,
+                                 size_t n, double* __restrict__ part) {
+  __shared__ double sh[BT];
+  const int j = blockIdx.y;
+  const double* v = V + j * ld;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)BT + threadIdx.x; i < n; i += (size_t)gridDim.x * BT) acc += v[i] * w[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = BT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// fixed-order final sum of np partials per output
+__global__ void finish_sum(const double* __restrict__ part, int np, int nout, double* __restrict__ res) {
+  __shared__ double sh[BT];
+  for (int j = 0; j < nout; ++j) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += BT) acc += part[(size_t)j * np + i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = BT / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) res[j] = sh[0];
+    __syncthreads();
+  }
+}
+
+__global__ void multiaxpy_kernel(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ c,
+                                 double* __restrict__ w, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < nv; ++j) acc -= c[j] * V[j * ld + i];
+    w[i] = acc;
+  }
+}
+
+__global__ void lincomb_kernel(const double* __restrict__ Z, size_t ld, int nv, const double* __restrict__ c,
+                               double* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < nv; ++j) acc += c[j] * Z[j * ld + i];
+    y[i] = acc;
+  }
+}
+
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void scale_inv_kernel(const double* __restrict__ x, const double* __restrict__ s, double* __restrict__ y,
+                                 size_t n) {
+  const double inv = 1.0 / s[0];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * inv;
+}
+
+}  // namespace
+
+cudaError_t cast_f64_f32(const double* x, float* y, size_t n, cudaStream_t s) {
+  cast_kernel<double, float><<<grid_for(n), BT, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t cast_f32_f64(const float* x, double* y, size_t n, cudaStream_t s) {
+  cast_kernel<float, double><<<grid_for(n), BT, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mass_apply(const st_problem* h, int level, const T* x, T* y, T* work) {
+  const Level& L = h->lev[level];
+  const int d = h->dim, K1 = h->K1;
+  double* bs = h->d_scratch + 2048;  // tau*w_mu per time node (set below)
+  double tw[MAX_K1];
+  for (int i = 0; i < K1; ++i) tw[i] = h->P.dt * h->T.w[i];
+  cudaError_t e = cudaMemcpyAsync(bs, tw, K1 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return e;
+  const double* M = h->R.M1;
+  T* t1 = work;
+  T* t2 = work + L.Nst;
+  // velocity: K1*d blocks of Nq2 on the Q2 grid; pressure: K1 blocks on the Q1 grid
+  for (int part = 0; part < 2; ++part) {
+    const long* g = part == 0 ? L.g2 : L.g1;
+    const long npt = g[0] * g[1] * g[2];
+    const int nblk = part == 0 ? K1 * d : K1;
+    const size_t off = part == 0 ? 0 : (size_t)K1 * L.Mv;
+    const T* src = x + off;
+    T* bufs[2] = {t1 + off, t2 + off};
+    for (int dir = 0; dir < d; ++dir) {
+      T* dst = (dir == d - 1) ? y + off : bufs[dir & 1];
+      const double* sc = (dir == d - 1) ? bs : nullptr;
+      const int cpn = part == 0 ? d : 1;
+      const long total = npt * nblk;
+      unsigned grid = (unsigned)((total + BT - 1) / BT);
+      if (grid > 152 * 16) grid = 152 * 16;
+      if (part == 0)
+        mass_pass<T, 2><<<grid, BT, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, L.h[dir], nblk, sc, cpn,
+                                                     (T)M[0], (T)M[1], (T)M[2], (T)M[4], (T)M[5], (T)M[8]);
+      else
+        mass_pass<T, 1><<<grid, BT, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, L.h[dir], nblk, sc, cpn,
+                                                     (T)(1.0 / 3.0), (T)(1.0 / 6.0), (T)0, (T)0, (T)0, (T)0);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      src = dst;
+    }
+  }
+  return cudaSuccess;
+}
+
+template cudaError_t mass_apply<double>(const st_problem*, int, const double*, double*, double*);
+template cudaError_t mass_apply<float>(const st_problem*, int, const float*, float*, float*);
+
+cudaError_t dot_f64(const double* x, const double* y, size_t n, double* dres, double* partial, cudaStream_t s) {
+  partial_dot<<<NPART, BT, 0, s>>>(x, y, n, partial);
+  finish_sum<<<1, BT, 0, s>>>(partial, NPART, 1, dres);
+  return cudaGetLastError();
+}
+
+cudaError_t multidot_f64(const double* V, size_t ld, int nv, const double* w, size_t n, double* dres, double* partial,
+                         cudaStream_t s) {
+  if (nv <= 0) return cudaSuccess;
+  const int np = 128;
+  partial_multidot<<<dim3(np, nv), BT, 0, s>>>(V, ld, nv, w, n, partial);
+  finish_sum<<<1, BT, 0, s>>>(partial, np, nv, dres);
+  return cudaGetLastError();
+}
+
+cudaError_t multiaxpy_f64(const double* V, size_t ld, int nv, const double* c, double* w, size_t n, cudaStream_t s) {
+  multiaxpy_kernel<<<grid_for(n), BT, 0, s>>>(V, ld, nv, c, w, n);
+  return cudaGetLastError();
+}
+
+cudaError_t lincomb_f64(const double* Z, size_t ld, int nv, const double* c, double* y, size_t n, cudaStream_t s) {
+  lincomb_kernel<<<grid_for(n), BT, 0, s>>>(Z, ld, nv, c, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t axpby_f64(double a, const double* x, double b, double* y, size_t n, cudaStream_t s) {
+  axpby_kernel<<<grid_for(n), BT, 0, s>>>(a, x, b, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_inv_f64(const double* x, const double* sdev, double* y, size_t n, cudaStream_t s) {
+  scale_inv_kernel<<<grid_for(n), BT, 0, s>>>(x, sdev, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t mnorm2_f64(st_problem* h, int level, const double* r, double* out) {
+  const Level& L = h->lev[level];
+  double* Mr = h->d_work;
+  double* work = h->d_work + L.Nst;
+  cudaError_t e = mass_apply<double>(h, level, r, Mr, work);
+  if (e == cudaSuccess) e = dot_f64(r, Mr, L.Nst, h->d_scratch, h->d_scratch + 8, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->d_scratch, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
+}
+
+}  // namespace st

@@ -1,0 +1,143 @@
+// Internal declarations of the GB300 slab solver library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/st.h"
+
+namespace st {
+
+constexpr int MAX_K1 = 4;      // k <= 3
+constexpr int OP_THREADS = 128;
+
+// ---------------------------------------------------------------- tables
+// Mesh-independent 1D reference tables on [0,1] (computed on the host).
+struct RefTables {
+  double B[9];    // Q2 Lagrange basis (nodes 0, 1/2, 1) at the 3 Gauss points, [q][a]
+  double Bt[9];   // transpose [a][q]
+  double Dc[9];   // collocation derivative through the Gauss points, at the Gauss points [q][q']
+  double W[3];    // Gauss weights
+  double B1[6];   // Q1 basis at the Gauss points [q][a]
+  double E[6];    // Q2 basis at x = 0 and x = 1, [end][a]
+  double ED[6];   // d/dx of the Q2 basis at x = 0 and x = 1, [end][a]
+  double M1[9];   // 1D Q2 mass matrix on [0,1]
+  double P2[15];  // 1D Q2 prolongation: coarse basis at fine nodes 0, 1/4, .., 1, [i][a]
+  double P1[6];   // 1D Q1 prolongation at fine nodes 0, 1/2, 1, [i][a]
+};
+
+struct TimeTab {
+  int k;
+  double t[MAX_K1], w[MAX_K1];
+  double Kt[MAX_K1 * MAX_K1], mt[MAX_K1];
+  double lrep[MAX_K1];  // Lagrange basis at the slab midpoint (t_rep)
+};
+
+void make_ref_tables(RefTables& R);
+bool make_time_tables(int k, TimeTab& T);
+
+// ----------------------------------------------------------- kernel args
+struct OpArgs {
+  int n[3];
+  double h[3], ih[3];
+  long g2[3], g1[3];
+  long Nq2, Nq1, Mv, Mp;
+  double vol;              // cell volume
+  double Dd[3][9];         // collocation derivative along each direction, scaled by 1/h
+  double Ddt[3][9];        // its transpose
+  double M1d[3][9];        // 1D mass matrix scaled by h (residual mass terms)
+  double tw[MAX_K1];       // tau * w_mu
+  double KtV[MAX_K1 * MAX_K1];  // K_t * cell volume
+  double Kt[MAX_K1 * MAX_K1];
+  double mt[MAX_K1];
+  // colour class
+  int colour;
+  int cn[3], c0[3];
+  long col_start, ncol;
+  // physics
+  double p, delta, nu, nu_inf, sigma_max, gamma1, gamma2, q_sign, vbar;
+  double L[3];
+  unsigned dmask;
+  int inflow;
+  int tangent;
+  // data
+  const void* in;          // dU (Jacobian) or U (residual, linearise)
+  void* out;               // output slab vector
+  const void* vprev;
+  const void* f;
+  const void* cache;       // volume coefficient cache (T)
+  const void* fcache;      // face coefficient cache (T)
+  double* wcache;          // FP64 caches written by linearise
+  double* wfcache;
+  const int* face_off;     // boundary-face offset of every colour-ordered cell
+  int* err;                // device error flag
+};
+
+enum OpMode { OP_LIN = 0, OP_JAC = 1, OP_RES = 2 };
+
+template <int DIM> struct Dims {
+  static constexpr int NQ = DIM == 3 ? 27 : 9;
+  static constexpr int NC = DIM;
+  static constexpr int NP = DIM == 3 ? 8 : 4;
+  static constexpr int NL = NQ / 3;
+  static constexpr int NFQ = DIM == 3 ? 9 : 3;
+  static constexpr int NFP = DIM == 3 ? 4 : 2;
+  static constexpr int NS = DIM == 3 ? 6 : 3;          // symmetric tensor entries
+  static constexpr int NF_VOL = 2 + NS + NC;           // eta_w, c_w, A, -u w
+  static constexpr int NF_FACE = 2 + NS + NC + 5 + NS + 1;  // + negw pen1 pen2 etaDw betaDw, Dg, w
+  static constexpr int NE = NC * NQ + NP;              // element dofs per time node
+};
+
+// ------------------------------------------------------------- levels
+struct Level {
+  int n[3];
+  double h[3];
+  long g2[3], g1[3];
+  long Nq2, Nq1, Mv, Mp, Nst, ncells;
+  int cn[8][3], c0[8][3];
+  long col_start[9];
+  long nfaces;
+  int* d_face_off = nullptr;   // ncells+1
+  // Vanka / coarse operator storage (set up by the preconditioner)
+};
+
+}  // namespace st
+
+struct st_problem {
+  st_params P;
+  cudaStream_t stream;
+  int dim, K1, nsm;
+  st::RefTables R;
+  st::TimeTab T;
+  std::vector<st::Level> lev;  // 0 = coarsest
+  // linearisation (finest level)
+  int lin_tangent = -1;
+  bool lin_valid = false;
+  double* d_cache64 = nullptr;
+  double* d_fcache64 = nullptr;
+  float* d_cache32 = nullptr;
+  float* d_fcache32 = nullptr;
+  size_t cache_len = 0, fcache_len = 0;
+  int* d_err = nullptr;
+  double* d_scratch = nullptr;     // small reduction scratch
+  size_t scratch_len = 0;
+  double* d_work = nullptr;        // 3 finest-level slab vectors (mass operator work)
+  std::string last_error;
+  bool precond_valid = false;
+  int precond_prec = -1;
+  void* mg = nullptr;              // multigrid state (st_mg.cu)
+};
+
+namespace st {
+
+// operator launches (st_operator_*.cu)
+cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent, const void* in, void* out,
+                      const void* vprev, const void* f);
+void fill_op_args(const st_problem* h, int level, OpArgs& a);
+
+st_status set_error(st_problem* h, st_status s, const std::string& msg);
+st_status cuda_check(st_problem* h, cudaError_t e, const char* where);
+
+}  // namespace st

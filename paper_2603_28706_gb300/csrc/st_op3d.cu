@@ -1,0 +1,13 @@
+// Operator kernels, three space dimensions.
+#include "st_op_inst.cuh"
+
+namespace st {
+cudaError_t dispatch_op_3d(const st_problem* h, const Level& L, OpArgs& a, int mode, int prec, int tangent) {
+  return dispatch_op_dim<3>(h, L, a, mode, prec, tangent);
+}
+cudaError_t upload_consts_3d(const ConstTables& t, const ConstTablesF& tf) {
+  cudaError_t e = cudaMemcpyToSymbol(cT, &t, sizeof(t));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(cTf, &tf, sizeof(tf));
+}
+}  // namespace st
