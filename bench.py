@@ -1,0 +1,304 @@
+"""Benchmark: matrix-free space-time Jacobian action, DoFs/s, 3D 32^3 Q2/Q1 dG(1).
+
+Workload (the metric's configuration): unit cube, 32^3 hexes, Q2/Q1, dG(1) with
+2 Radau points, p = 1.3, delta = 1e-4, nu = 1e-3, nu_inf = 1e-4, smooth random
+velocity (8 Fourier modes), uniform random pressure and increment.  One step =
+for each of Pic, exN, modN: one FP64 linearisation + 100 FP64 Jacobian applies.
+value = space-time DoFs x applies / second, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 oracle on the host cores (bounded sample of
+cells per step).  Under torchrun (N > 1) every rank runs an independent
+replica (the single-slab apply has no data-parallel split); value sums the
+ranks' DoFs over the max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import st_inputs as si  # noqa: E402
+
+METRIC = "Jacobian-apply space-time DoFs/s + % roofline; mixed vs FP64 Newton-step time at 1e-8"
+UNIT = "DoF/s"
+APPLIES = 100
+TANGENT_NAMES = ["pic", "exn", "modn"]
+WORKLOAD = "3D unit cube 32^3 hexes, Q2/Q1, dG(1) 2 Radau points, p=1.3, delta=1e-4, nu_inf=1e-4; " \
+           "100 FP64 Jacobian applies each for exN, modN, Pic"
+
+
+def flops_per_apply(p):
+    """Algorithmic FP64 flops of one Jacobian apply of the sum-factorised
+    kernel (FMA = 2 flops), per cell-node and per boundary face-node."""
+    K1 = p["k"] + 1
+    if p["dim"] == 3:
+        vol = 1215 + 1215 + 162 * K1 + 2106 + 1458 + 424 + 1215
+        face = 3600
+        nx, ny, nz = p["nx"], p["ny"], p["nz"]
+        nfaces = 2 * (nx * ny + ny * nz + nx * nz)
+        ncells = nx * ny * nz
+    else:
+        vol = 270 + 180 + 36 * K1 + 9 * 40 + 180 + 4 * 17 + 180
+        face = 400
+        nfaces = 2 * (p["nx"] + p["ny"])
+        ncells = p["nx"] * p["ny"]
+    return K1 * (ncells * vol + nfaces * face)
+
+
+def bytes_per_apply(p):
+    """Algorithmic HBM bytes of one FP64 apply: dU read, out read+write
+    (scatter-add), coefficient cache read."""
+    s = si.sizes(p)
+    K1 = p["k"] + 1
+    ncells = p["nx"] * p["ny"] * (p["nz"] if p["dim"] == 3 else 1)
+    nq, nf = (27, 11) if p["dim"] == 3 else (9, 7)
+    return 8 * (3 * s["Nst"] + ncells * K1 * nq * nf)
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+            "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+            "clocks_event_reasons.sw_power_cap"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(p, U, dU, ncells_sample, seed=0):
+    """The FP64 oracle's Jacobian apply on a sample of cells, all tangents."""
+    import oracle
+    ncells = p["nx"] * p["ny"] * p["nz"]
+    rng = np.random.default_rng(seed)
+    cells = np.sort(rng.choice(ncells, size=ncells_sample, replace=False))
+    t0 = time.perf_counter()
+    for var in (oracle.PIC, oracle.EXN, oracle.MODN):
+        oracle.jacobian_apply(p, var, U, dU, cells=cells)
+    dt = time.perf_counter() - t0
+    dofs = 3 * si.sizes(p)["Nst"] * ncells_sample / ncells
+    return dofs / dt, dt, oracle.lib().or_num_threads()
+
+
+def run_reference(args, p, U, dU):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sample = int(os.environ.get("ST_ORACLE_SAMPLE_CELLS", "1024"))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(p, U, dU, max(64, sample // 8))
+    times, rates = [], []
+    cores = None
+    for i in range(args.steps):
+        r, dt, cores = cpu_oracle_rate(p, U, dU, sample, seed=i)
+        times.append(dt)
+        rates.append(r)
+    total_dofs = sum(r * t for r, t in zip(rates, times))
+    value = total_dofs / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "%d of 32768 cells per step, 3 tangents" % sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d random cells of the 32^3 mesh per step (element matrices formed and "
+                                       "applied per call), Pic+exN+modN" % sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    p, U, dU, vp = si.workload(2)
+    if args.impl == "reference":
+        return run_reference(args, p, U, dU)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2603_28706_gb300 as st
+    st.build.build()
+    stream = torch.cuda.current_stream()
+    prob = st.Problem(p, stream=stream)
+    n = prob.num_dofs()
+    Ud = torch.from_numpy(U).cuda()
+    dUd = torch.from_numpy(dU).cuda()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    tangents = [st.ST_PIC, st.ST_EXN, st.ST_MODN]
+
+    def step():
+        for tg in tangents:
+            prob.linearize(tg, Ud)
+            for _ in range(APPLIES):
+                prob.jacobian_apply(tg, dUd, out=out)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    applies = args.steps * len(tangents) * APPLIES
+    value = ws * n * applies / (ms * 1e-3)
+
+    # dominant kernel: the FP64 Jacobian apply, timed alone with events on its stream
+    prob.linearize(st.ST_MODN, Ud)
+    for _ in range(3):
+        prob.jacobian_apply(st.ST_MODN, dUd, out=out)
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    reps = 50
+    r0.record(stream)
+    for _ in range(reps):
+        prob.jacobian_apply(st.ST_MODN, dUd, out=out)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = r0.elapsed_time(r1) / reps
+    fl = flops_per_apply(p)
+    peak = 152 * 2 * 2 * 2.070e9 / 1e12  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz
+    achieved = fl / (apply_ms * 1e-3) / 1e12
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("st_op_kernel_jac_fp64_per_apply")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "st_op_kernel<3,2,double,OP_JAC,1> (8 colour launches per apply)",
+                "apply_ms": apply_ms, "flops_per_apply": fl, "algorithmic_bytes_per_apply": bytes_per_apply(p),
+                "hbm_frac_of_measured": bytes_per_apply(p) / (apply_ms * 1e-3) / 6771.1e9}
+
+    # end to end through the public API with pinned host buffers
+    Uh = torch.from_numpy(U).pin_memory()
+    dUh = torch.from_numpy(dU).pin_memory()
+    outh = torch.empty(n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 2))
+    h0.record(stream)
+    for _ in range(e2e_steps):
+        for tg in tangents:
+            Ud.copy_(Uh, non_blocking=True)
+            dUd.copy_(dUh, non_blocking=True)
+            prob.linearize(tg, Ud)
+            for _ in range(APPLIES):
+                prob.jacobian_apply(tg, dUd, out=out)
+            outh.copy_(out, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = h0.elapsed_time(h1) / e2e_steps
+    e2e = {"value": ws * n * len(tangents) * APPLIES / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": len(tangents) * 2 * 8 * n, "d2h_bytes_per_step": len(tangents) * 8 * n}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sample = int(os.environ.get("ST_ORACLE_SAMPLE_CELLS", "2048"))
+        rate, dt, cores = cpu_oracle_rate(p, U, dU, sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d random cells of the 32^3 mesh (element matrices formed and applied), Pic+exN+modN, "
+                         "%.1f s" % (sample, dt)}
+    ncol = 8
+    launches_per_step = len(tangents) * ((ncol + 2) + APPLIES * ncol)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "dofs": n, "applies_per_step": len(tangents) * APPLIES,
+                           "l2": "inputs larger than L2 (coefficient cache %.0f MB + vectors)" %
+                                 (8 * 2 * 32768 * 27 * 11 / 1e6),
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
+                "clocks": clk.summary()}
+        print(json.dumps(line))
+    prob.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -109,25 +109,26 @@ void make_level(const st_params& P, int nx, int ny, int nz, Level& L) {
   }
 }
 
-// boundary-face offsets of colour-ordered cells: faces of a cell are its
-// boundary sides in increasing side order
-std::vector<int> face_offsets(const st_params& P, const Level& L, long& nfaces) {
+// boundary faces in linear cell order, each cell's boundary sides in
+// increasing side order: offsets per cell, cell and side per face
+std::vector<int> face_lists(const st_params& P, Level& L, std::vector<int>& fcell, std::vector<unsigned char>& fside) {
   const int d = P.dim;
   std::vector<int> off(L.ncells + 1, 0);
-  long acc = 0;
-  for (int c = 0; c < (1 << d); ++c) {
-    const long n0 = L.col_start[c], ncol = L.col_start[c + 1] - n0;
-    for (long li = 0; li < ncol; ++li) {
-      const int i = (int)(li % L.cn[c][0]);
-      const int j = (int)((li / L.cn[c][0]) % L.cn[c][1]);
-      const int l = (int)(li / ((long)L.cn[c][0] * L.cn[c][1]));
-      const int e3[3] = {L.c0[c][0] + 2 * i, L.c0[c][1] + 2 * j, d == 3 ? L.c0[c][2] + 2 * l : 0};
-      off[n0 + li] = (int)acc;
-      for (int ax = 0; ax < d; ++ax) acc += (e3[ax] == 0) + (e3[ax] == L.n[ax] - 1);
+  fcell.clear();
+  fside.clear();
+  for (long cell = 0; cell < L.ncells; ++cell) {
+    const int e3[3] = {(int)(cell % L.n[0]), (int)((cell / L.n[0]) % L.n[1]), (int)(cell / ((long)L.n[0] * L.n[1]))};
+    off[cell] = (int)fcell.size();
+    for (int sd = 0; sd < 2 * d; ++sd) {
+      const int ax = sd >> 1, up = sd & 1;
+      const bool on = up ? (e3[ax] == L.n[ax] - 1) : (e3[ax] == 0);
+      if (!on) continue;
+      fcell.push_back((int)cell);
+      fside.push_back((unsigned char)sd);
     }
   }
-  off[L.ncells] = (int)acc;
-  nfaces = acc;
+  off[L.ncells] = (int)fcell.size();
+  L.nfaces = (long)fcell.size();
   return off;
 }
 
@@ -270,10 +271,21 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
   for (int l = 0; l < nl; ++l) {
     const int sh = nl - 1 - l;
     make_level(*params, params->nx >> sh, params->ny >> sh, params->dim == 3 ? (params->nz >> sh) : 1, h->lev[l]);
-    std::vector<int> off = face_offsets(*params, h->lev[l], h->lev[l].nfaces);
-    e = cudaMalloc(&h->lev[l].d_face_off, off.size() * sizeof(int));
+    std::vector<int> fcell;
+    std::vector<unsigned char> fside;
+    std::vector<int> off = face_lists(*params, h->lev[l], fcell, fside);
+    if (fcell.empty()) {
+      fcell.push_back(0);
+      fside.push_back(0);
+    }
+    Level& Lv = h->lev[l];
+    e = cudaMalloc(&Lv.d_face_off, off.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(Lv.d_face_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&Lv.d_face_cell, fcell.size() * sizeof(int));
     if (e == cudaSuccess)
-      e = cudaMemcpy(h->lev[l].d_face_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+      e = cudaMemcpy(Lv.d_face_cell, fcell.data(), fcell.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&Lv.d_face_side, fside.size());
+    if (e == cudaSuccess) e = cudaMemcpy(Lv.d_face_side, fside.data(), fside.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       st_destroy(h);
       return e == cudaErrorMemoryAllocation ? ST_ENOMEM : ST_ECUDA;
@@ -293,6 +305,14 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 16 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, h->scratch_len * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_work, 3 * (size_t)F.Nst * sizeof(double));
+  {
+    const int nout = h->dim == 3 ? 2 * 3 * 9 + 4 : 2 * 2 * 3 + 2;
+    const size_t nf = (size_t)(F.nfaces > 0 ? F.nfaces : 1) * h->K1 * nout;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_fscr, nf * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_face, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 16 * sizeof(int), h->stream);
   if (e != cudaSuccess) {
     st_destroy(h);
@@ -305,7 +325,11 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
 st_status st_destroy(st_problem* h) {
   if (!h) return ST_OK;
   mg_destroy(h);
-  for (auto& L : h->lev) cudaFree(L.d_face_off);
+  for (auto& L : h->lev) {
+    cudaFree(L.d_face_off);
+    cudaFree(L.d_face_cell);
+    cudaFree(L.d_face_side);
+  }
   cudaFree(h->d_cache64);
   cudaFree(h->d_fcache64);
   cudaFree(h->d_cache32);
@@ -313,6 +337,10 @@ st_status st_destroy(st_problem* h) {
   cudaFree(h->d_err);
   cudaFree(h->d_scratch);
   cudaFree(h->d_work);
+  cudaFree(h->d_fscr);
+  if (h->s_face) cudaStreamDestroy(h->s_face);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return ST_OK;
 }

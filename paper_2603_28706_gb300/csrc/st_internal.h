@@ -71,7 +71,7 @@ struct OpArgs {
   const void* fcache;      // face coefficient cache (T)
   double* wcache;          // FP64 caches written by linearise
   double* wfcache;
-  const int* face_off;     // boundary-face offset of every colour-ordered cell
+  const int* face_off;     // first boundary face of every cell (linear order)
   int* err;                // device error flag
 };
 
@@ -99,7 +99,9 @@ struct Level {
   int cn[8][3], c0[8][3];
   long col_start[9];
   long nfaces;
-  int* d_face_off = nullptr;   // ncells+1
+  int* d_face_off = nullptr;   // ncells+1: first boundary face of every (linear) cell
+  int* d_face_cell = nullptr;  // nfaces: linear cell of each boundary face
+  unsigned char* d_face_side = nullptr;  // nfaces: side (2*axis + upper) of each boundary face
   // Vanka / coarse operator storage (set up by the preconditioner)
 };
 
@@ -124,6 +126,9 @@ struct st_problem {
   double* d_scratch = nullptr;     // small reduction scratch
   size_t scratch_len = 0;
   double* d_work = nullptr;        // 3 finest-level slab vectors (mass operator work)
+  double* d_fscr = nullptr;         // compact per-face-slot outputs of the face kernel (FP64 or FP32 view)
+  cudaStream_t s_face = nullptr;   // internal stream: face kernels overlap the volume kernels
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string last_error;
   bool precond_valid = false;
   int precond_prec = -1;

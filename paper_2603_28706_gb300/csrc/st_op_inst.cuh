@@ -1,6 +1,7 @@
 // Launch helpers for the operator kernels of one dimension.
 #pragma once
 
+#include "st_face.cuh"
 #include "st_operator.cuh"
 
 namespace st {
@@ -8,12 +9,40 @@ namespace st {
 template <int DIM, int K1, typename T, int MODE, int TAN>
 cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   using Cfg = OpCfg<DIM, K1, T>;
+  using FCfg = FaceCfg<DIM, T>;
   auto kern = st_op_kernel<DIM, K1, T, MODE, TAN>;
-  static bool attr_done = false;
-  if (!attr_done) {
+  auto fkern = st_face_kernel<DIM, K1, T, MODE, TAN>;
+  static int occ = 0, focc = 0;
+  if (occ == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FCfg::smem_bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::NT, Cfg::smem_bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fkern, OP_THREADS, FCfg::smem_bytes);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    if (occ < 1) occ = 1;
+    if (focc < 1) focc = 1;
+  }
+  // The face kernel (all boundary faces, one launch) runs on an internal
+  // stream concurrently with the volume kernels; it writes only the face
+  // scratch (or, when linearising, the face cache).  The volume kernels run
+  // colour by colour on the caller's stream and scatter-add into `out`.  The
+  // caller's stream then waits for the face kernel and st_face_gather adds the
+  // face contributions into `out`, one thread per node.
+  cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
+  if (e != cudaSuccess) return e;
+  T* fscr = reinterpret_cast<T*>(h->d_fscr);
+  const long nslots = L.nfaces * K1;
+  if (nslots > 0) {
+    long fgrid = (nslots + FCfg::FS - 1) / FCfg::FS;
+    const long fcap = 8L * h->nsm;
+    if (fgrid > fcap) fgrid = fcap;
+    fkern<<<(unsigned)fgrid, OP_THREADS, FCfg::smem_bytes, h->s_face>>>(a, L.d_face_cell, L.d_face_side, nslots,
+                                                                         fscr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   const int ncolours = 1 << DIM;
   for (int c = 0; c < ncolours; ++c) {
@@ -26,16 +55,28 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
     }
     a.col_start = L.col_start[c];
     a.ncol = ncol;
-    // two resident CTAs per SM; each CTA at least half a batch of cells
-    long grid = (ncol + Cfg::C / 2 - 1) / (Cfg::C / 2 > 0 ? Cfg::C / 2 : 1);
-    const long cap = 2L * h->nsm;
+    // every resident CTA slot gets an equal share of the colour class when there
+    // is at least half a batch per slot; smaller classes use full batches
+    const long cap = (long)occ * h->nsm;
+    long grid = (ncol + Cfg::C - 1) / Cfg::C;
+    if (ncol >= cap * (Cfg::C / 2)) grid = cap;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, OP_THREADS, Cfg::smem_bytes, h->stream>>>(a);
-    cudaError_t e = cudaGetLastError();
+    kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  e = cudaEventRecord(h->ev_join, h->s_face);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+  if (e != cudaSuccess) return e;
+  if (MODE != OP_LIN && nslots > 0) {
+    const long nn = L.Nq2 + L.Nq1;
+    long g = (nn + 255) / 256;
+    if (g > 16L * h->nsm) g = 16L * h->nsm;
+    st_face_gather<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(a, L.d_face_off, fscr, reinterpret_cast<T*>(a.out));
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <int DIM, int K1>

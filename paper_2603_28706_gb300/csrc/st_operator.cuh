@@ -12,15 +12,22 @@
 //   OP_RES: out += R_n(U) (eq. slab-underint, eq. disc, def-a-gam, def-b-gam).
 //
 // Work decomposition: a CTA owns a contiguous, balanced chunk of the colour
-// class and processes it in batches of C cells.  A batch holds C*(k+1)
-// "slots" (cell, Radau node) in shared memory.  Every stage of the
-// sum-factorised evaluation is a flat list of independent items (one 3-point
-// line of a slot, or one quadrature point of a slot) spread over all threads,
-// so all lanes carry work; stages are separated by __syncthreads.
-//   gather -> 3 value passes (Q2 basis at Gauss points) -> derivative passes
-//   in collocation form -> pointwise flux at every quadrature point ->
-//   transposed derivative chain -> 3 transposed value passes -> boundary faces
-//   (in rounds, one face per slot per round) -> scatter-add.
+// class and processes it in batches of C cells, i.e. C*(k+1) "slots" (cell,
+// Radau node) held in shared memory.  Stages (separated by __syncthreads):
+//   S0  gather the nodal values of every slot (coalesced over slots);
+//   S1  per (slot, component), in registers: values at the 3^d Gauss points
+//       (one pass of the 3x3 Q2 basis matrix per direction) and the gradient in
+//       collocation form (one pass of the collocation derivative per direction);
+//   S3  per (slot, quadrature point): the pointwise work (coefficient cache,
+//       tangent, convection, pressure; residual stress law) -> gradient-test
+//       fluxes in place, pressure-test flux;
+//   S4  per (slot, component), in registers: the K_t (x) M_x value term, the
+//       transposed derivative chain and transposed value passes, then the
+//       scatter-add straight from registers; per (slot, pressure node): the
+//       pressure test.
+// All FP64 arithmetic of S1/S4 runs on register-resident 3^d blocks with
+// nine independent FMA chains per pass.  Boundary-face terms are a separate
+// kernel (st_face.cuh) launched after the volume kernel of the same colour.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -129,24 +136,97 @@ __device__ __forceinline__ void lifting(const OpArgs& a, const double x[3], doub
   grad[2] = a.vbar * fy * dfz;
 }
 
+// asynchronous element copy global -> shared (Ampere+ cp.async, 4 or 8 bytes)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(gmem_src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// compile-time geometry of the 3-point lines of a 3^DIM block
+template <int DIM, int DIR>
+__device__ __forceinline__ constexpr int lbase(int l) {
+  return DIM == 2 ? (DIR == 0 ? 3 * l : l) : (DIR == 0 ? 3 * l : (DIR == 1 ? (l % 3) + 9 * (l / 3) : l));
+}
+template <int DIR>
+__device__ __forceinline__ constexpr int lstride() {
+  return DIR == 0 ? 1 : (DIR == 1 ? 3 : 9);
+}
+
+// in-place pass of a register array along DIR: v <- M v on every line
+template <int DIM, int DIR, typename T, typename MT>
+__device__ __forceinline__ void rpass(T* v, const MT* m) {
+  constexpr int NL = Dims<DIM>::NL, st = lstride<DIR>();
+  const T m0 = (T)m[0], m1 = (T)m[1], m2 = (T)m[2], m3 = (T)m[3], m4 = (T)m[4], m5 = (T)m[5], m6 = (T)m[6],
+          m7 = (T)m[7], m8 = (T)m[8];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int b = lbase<DIM, DIR>(l);
+    const T x0 = v[b], x1 = v[b + st], x2 = v[b + 2 * st];
+    v[b] = m0 * x0 + m1 * x1 + m2 * x2;
+    v[b + st] = m3 * x0 + m4 * x1 + m5 * x2;
+    v[b + 2 * st] = m6 * x0 + m7 * x1 + m8 * x2;
+  }
+}
+
+// dst <- M v along DIR (dst in shared memory)
+template <int DIM, int DIR, typename T, typename MT>
+__device__ __forceinline__ void rpass_out(const T* v, const MT* m, T* dst) {
+  constexpr int NL = Dims<DIM>::NL, st = lstride<DIR>();
+  const T m0 = (T)m[0], m1 = (T)m[1], m2 = (T)m[2], m3 = (T)m[3], m4 = (T)m[4], m5 = (T)m[5], m6 = (T)m[6],
+          m7 = (T)m[7], m8 = (T)m[8];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int b = lbase<DIM, DIR>(l);
+    const T x0 = v[b], x1 = v[b + st], x2 = v[b + 2 * st];
+    dst[b] = m0 * x0 + m1 * x1 + m2 * x2;
+    dst[b + st] = m3 * x0 + m4 * x1 + m5 * x2;
+    dst[b + 2 * st] = m6 * x0 + m7 * x1 + m8 * x2;
+  }
+}
+
+// acc <- acc + M g along DIR (g in shared memory)
+template <int DIM, int DIR, typename T, typename MT>
+__device__ __forceinline__ void rpass_acc(T* acc, const MT* m, const T* g) {
+  constexpr int NL = Dims<DIM>::NL, st = lstride<DIR>();
+  const T m0 = (T)m[0], m1 = (T)m[1], m2 = (T)m[2], m3 = (T)m[3], m4 = (T)m[4], m5 = (T)m[5], m6 = (T)m[6],
+          m7 = (T)m[7], m8 = (T)m[8];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int b = lbase<DIM, DIR>(l);
+    const T x0 = g[b], x1 = g[b + st], x2 = g[b + 2 * st];
+    acc[b] += m0 * x0 + m1 * x1 + m2 * x2;
+    acc[b + st] += m3 * x0 + m4 * x1 + m5 * x2;
+    acc[b + 2 * st] += m6 * x0 + m7 * x1 + m8 * x2;
+  }
+}
+
 template <int DIM, int K1, typename T>
 struct OpCfg {
   using D = Dims<DIM>;
-  static constexpr int C = DIM == 3 ? ((sizeof(T) == 8 ? 28 : 48) / K1) : (96 / K1);
+  static constexpr int NT = DIM == 3 ? 96 : 128;       // threads per CTA
+  static constexpr int SLOTS = DIM == 3 ? 32 : 64;     // target (cell, node) slots per batch
+  static constexpr int C = SLOTS / K1 > 0 ? SLOTS / K1 : 1;
   static constexpr int S = C * K1;
-  // per-slot shared arrays (elements of T)
+  // per-slot shared arrays (elements of T): qp values, gradients/fluxes, nodal pressure, pressure-test flux
   static constexpr int SX = D::NC * D::NQ;
   static constexpr int SG = D::NC * DIM * D::NQ;
   static constexpr int SP = D::NP;
-  static constexpr int per_slot = SX + SG + SP + SX + SP;
-  static constexpr size_t smem_bytes = (size_t)S * per_slot * sizeof(T) + (size_t)S * 4 * sizeof(int) + 64;
+  static constexpr int SQ = D::NQ;
+  static constexpr int per_slot = SX + SG + SP + SQ;
+  static constexpr size_t smem_bytes = (size_t)S * per_slot * sizeof(T) + (size_t)C * sizeof(int) + 64;
 };
 
 template <int DIM, int K1, typename T, int MODE, int TAN>
-__global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
+__global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpArgs a) {
   using D = Dims<DIM>;
   using Cfg = OpCfg<DIM, K1, T>;
-  constexpr int NQ = D::NQ, NC = D::NC, NP = D::NP, NL = D::NL, NFQ = D::NFQ, NS = D::NS;
+  constexpr int NQ = D::NQ, NC = D::NC, NP = D::NP, NS = D::NS;
   constexpr int C = Cfg::C, S = Cfg::S;
   const auto& ct = CT<T>::t();
 
@@ -154,14 +234,8 @@ __global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
   T* sX = reinterpret_cast<T*>(smem_raw);
   T* sG = sX + S * Cfg::SX;
   T* sP = sG + S * Cfg::SG;
-  T* sO = sP + S * Cfg::SP;   // TV, then velocity output
-  T* sOp = sO + S * Cfg::SX;  // pressure output
-  int* sCell = reinterpret_cast<int*>(sOp + S * Cfg::SP);  // linear cell id of batch cell
-  int* sFside = sCell + S;    // per slot: side of the face in this round
-  int* sFid = sFside + S;     // per slot: face id
-  int* sAct = sFid + S;       // compacted list of slots with a face
-  __shared__ int sNact;
-  __shared__ int sBfaces;     // max number of boundary faces of a batch cell
+  T* sQ = sP + S * Cfg::SP;
+  int* sCell = reinterpret_cast<int*>(sQ + S * Cfg::SQ);  // linear cell id of batch cell
 
   const T* in = reinterpret_cast<const T*>(a.in);
   T* out = reinterpret_cast<T*>(a.out);
@@ -171,9 +245,7 @@ __global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
   const long cbeg = (long)blockIdx.x * ncol / gridDim.x;
   const long cend = (long)(blockIdx.x + 1) * ncol / gridDim.x;
 
-  const T* Dd[3] = {nullptr, nullptr, nullptr};
-  const T* Ddt[3] = {nullptr, nullptr, nullptr};
-  // scaled derivative matrices in the precision of the kernel
+  // scaled derivative and mass matrices in the precision of the kernel
   __shared__ T sDd[3][9], sDdt[3][9], sM1[3][9];
   if (threadIdx.x < 27) {
     const int d = threadIdx.x / 9, e = threadIdx.x % 9;
@@ -181,19 +253,13 @@ __global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
     sDdt[d][e] = (T)a.Ddt[d][e];
     sM1[d][e] = (T)a.M1d[d][e];
   }
-  for (int d = 0; d < 3; ++d) {
-    Dd[d] = sDd[d];
-    Ddt[d] = sDdt[d];
-  }
   __syncthreads();
 
   for (long b0 = cbeg; b0 < cend; b0 += C) {
     const int nc = (int)min((long)C, cend - b0);
     const int ns = nc * K1;
 
-    // ---- batch setup: cell ids, boundary-face counts
-    if (threadIdx.x == 0) sBfaces = 0;
-    __syncthreads();
+    // ---- batch setup: cell ids
     for (int ci = threadIdx.x; ci < nc; ci += blockDim.x) {
       const long li = b0 + ci;  // index within the colour class
       const int i = (int)(li % a.cn[0]);
@@ -201,79 +267,64 @@ __global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
       const int l = (int)(li / ((long)a.cn[0] * a.cn[1]));
       const int ex = a.c0[0] + 2 * i, ey = a.c0[1] + 2 * j, ez = (DIM == 3) ? a.c0[2] + 2 * l : 0;
       sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
-      int nb = 0;
-      const int e3[3] = {ex, ey, ez};
-      for (int ax = 0; ax < DIM; ++ax) nb += (e3[ax] == 0) + (e3[ax] == a.n[ax] - 1);
-      atomicMax(&sBfaces, nb);
     }
     __syncthreads();
 
-    // ---- S0: gather nodal values of every slot (velocity, pressure)
+    // ---- S0: gather nodal values of every slot (velocity, pressure) with
+    //      asynchronous global->shared copies (all loads of the batch in flight);
+    //      prefetch the batch's coefficient-cache block into L2 meanwhile
     for (int it = threadIdx.x; it < ns * (NC * NQ + NP); it += blockDim.x) {
       const int s = it / (NC * NQ + NP), r = it % (NC * NQ + NP);
       const int ci = s / K1, mu = s % K1;
       const int cell = sCell[ci];
       const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+      const T* src;
+      T* dst;
       if (r < NC * NQ) {
         const int c = r / NQ, q = r % NQ;
         const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
         const long g = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz));
-        sX[s * Cfg::SX + r] = in[(long)mu * a.Mv + c * a.Nq2 + g];
+        src = in + (long)mu * a.Mv + c * a.Nq2 + g;
+        dst = sX + s * Cfg::SX + r;
       } else {
         const int m = r - NC * NQ;
         const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
         const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
-        sP[s * NP + m] = in[(long)K1 * a.Mv + (long)mu * a.Mp + g];
+        src = in + (long)K1 * a.Mv + (long)mu * a.Mp + g;
+        dst = sP + s * NP + m;
       }
+      cp_async_elem<T>(dst, src);
     }
+    cp_async_commit();
+    if constexpr (MODE == OP_JAC) {
+      const char* cb = reinterpret_cast<const char*>(a.cache) +
+                       (size_t)(a.col_start + b0) * K1 * D::NF_VOL * NQ * sizeof(T);
+      const size_t nbytes = (size_t)ns * D::NF_VOL * NQ * sizeof(T);
+      for (size_t off = (size_t)threadIdx.x * 128; off < nbytes; off += (size_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cb + off));
+    }
+    cp_async_wait_all();
     __syncthreads();
 
-    // ---- S1: values at the Gauss points, one pass per direction (in place)
-    for (int dir = 0; dir < DIM; ++dir) {
-      for (int it = threadIdx.x; it < ns * NC * NL; it += blockDim.x) {
-        const int s = it / (NC * NL), r = it % (NC * NL);
-        T* x = sX + s * Cfg::SX + (r / NL) * NQ;
-        line_pass<DIM, T>(x, dir, r % NL, ct.B, x);
-      }
-      __syncthreads();
+    // ---- S1: per (slot, component), in registers: values at the Gauss points
+    //      (Q2 basis, one pass per direction), then the gradient in collocation form
+    for (int it = threadIdx.x; it < ns * NC; it += blockDim.x) {
+      const int s = it / NC, c = it % NC;
+      T* xs = sX + s * Cfg::SX + c * NQ;
+      T v[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = xs[q];
+      rpass<DIM, 0>(v, ct.B);
+      rpass<DIM, 1>(v, ct.B);
+      if constexpr (DIM == 3) rpass<DIM, 2>(v, ct.B);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) xs[q] = v[q];
+      T* gs = sG + s * Cfg::SG + c * DIM * NQ;
+      rpass_out<DIM, 0>(v, sDd[0], gs);
+      rpass_out<DIM, 1>(v, sDd[1], gs + NQ);
+      if constexpr (DIM == 3) rpass_out<DIM, 2>(v, sDd[2], gs + 2 * NQ);
     }
-
-    // ---- S2: gradients in collocation form; time mixing of the values (JAC)
-    {
-      const int n_grad = ns * NC * DIM * NL;
-      const int n_mix = (MODE == OP_JAC) ? nc * NC * NQ : 0;
-      for (int it = threadIdx.x; it < n_grad + n_mix; it += blockDim.x) {
-        if (it < n_grad) {
-          const int s = it / (NC * DIM * NL), r = it % (NC * DIM * NL);
-          const int c = r / (DIM * NL), dir = (r / NL) % DIM, l = r % NL;
-          const T* x = sX + s * Cfg::SX + c * NQ;
-          T* g = sG + s * Cfg::SG + (c * DIM + dir) * NQ;
-          int b, st;
-          line_idx<DIM>(dir, l, b, st);
-          T y0, y1, y2;
-          apply3<T, T>(Dd[dir], x[b], x[b + st], x[b + 2 * st], y0, y1, y2);
-          g[b] = y0;
-          g[b + st] = y1;
-          g[b + 2 * st] = y2;
-        } else {
-          // tv_i(q) = W(q) sum_j (K_t vol)_ij du_j(q): the K_t (x) M_x block at the quadrature points
-          const int r = it - n_grad;
-          const int ci = r / (NC * NQ), c = (r / NQ) % NC, q = r % NQ;
-          T xj[K1];
-#pragma unroll
-          for (int j = 0; j < K1; ++j) xj[j] = sX[(ci * K1 + j) * Cfg::SX + c * NQ + q];
-          const T wq = (DIM == 3) ? ct.WQ3[q] : ct.WQ2[q];
-#pragma unroll
-          for (int i = 0; i < K1; ++i) {
-            T sacc = (T)a.KtV[i * K1] * xj[0];
-#pragma unroll
-            for (int j = 1; j < K1; ++j) sacc += (T)a.KtV[i * K1 + j] * xj[j];
-            sO[(ci * K1 + i) * Cfg::SX + c * NQ + q] = sacc * wq;
-          }
-        }
-      }
-      __syncthreads();
-    }
+    __syncthreads();
 
     // ---- S3: pointwise work at every quadrature point of every slot
     for (int it = threadIdx.x; it < ns * NQ; it += blockDim.x) {
@@ -386,7 +437,7 @@ __global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
         for (int c = 0; c < NC; ++c)
 #pragma unroll
           for (int j = 0; j < DIM; ++j) sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = G[c][j];
-        sX[s * Cfg::SX + q] = -div * tw;  // pressure test flux (aliases the value array)
+        sQ[s * NQ + q] = -div * tw;  // pressure test flux
       } else {  // OP_RES: F = RHS - LHS, gradient-test flux -(S(Du) - u (x) u - pi I)
         const T* psi = (DIM == 3) ? &ct.PSI3[q * 8] : &ct.PSI2[q * 4];
         T pi = 0;
@@ -412,523 +463,88 @@ __global__ void __launch_bounds__(OP_THREADS) st_op_kernel(const OpArgs a) {
 #pragma unroll
           for (int j = 0; j < DIM; ++j)
             sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = -(eta * A[c][j] - u[c] * u[j] - (c == j ? pi : (T)0)) * tw;
-        sX[s * Cfg::SX + q] = div * tw;
+        sQ[s * NQ + q] = div * tw;
       }
     }
     __syncthreads();
 
     if constexpr (MODE != OP_LIN) {
-      // ---- integration: collocation-space sum of the derivative tests (chain)
-      for (int dir = 0; dir < DIM; ++dir) {
-        const int n_lines = ns * NC * NL;
-        const int n_pt = (dir == 0) ? ns * NP : 0;
-        for (int it = threadIdx.x; it < n_lines + n_pt; it += blockDim.x) {
-          if (it < n_lines) {
-            const int s = it / (NC * NL), r = it % (NC * NL);
-            const int c = r / NL, l = r % NL;
-            T* gsl = sG + s * Cfg::SG + (c * DIM + dir) * NQ;
-            if (dir == 0) {
-              if (MODE == OP_JAC) {
-                line_pass_acc<DIM, T>(gsl, 0, l, Ddt[0], sO + s * Cfg::SX + c * NQ, gsl);
-              } else {
-                line_pass<DIM, T>(gsl, 0, l, Ddt[0], gsl);
-              }
-            } else {
-              line_pass_acc<DIM, T>(gsl, dir, l, Ddt[dir], gsl - NQ, gsl);
+      // ---- S4: per (slot, component), in registers: K_t (x) M_x value term,
+      //      transposed derivative chain, transposed value passes, nodal value
+      //      terms (residual), scatter-add; per (slot, pressure node): pressure test
+      for (int it = threadIdx.x; it < ns * (NC + NP); it += blockDim.x) {
+        if (it < ns * NC) {
+          const int s = it / NC, c = it % NC;
+          const int ci = s / K1, mu = s % K1;
+          T acc[NQ];
+          if constexpr (MODE == OP_JAC) {
+            // tv_mu(q) = W(q) sum_j (K_t vol)_{mu j} du_j(q)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              T t = (T)a.KtV[mu * K1] * sX[(ci * K1) * Cfg::SX + c * NQ + q];
+#pragma unroll
+              for (int j = 1; j < K1; ++j) t += (T)a.KtV[mu * K1 + j] * sX[(ci * K1 + j) * Cfg::SX + c * NQ + q];
+              acc[q] = t * ((DIM == 3) ? ct.WQ3[q] : ct.WQ2[q]);
             }
           } else {
-            // pressure test: out_m = sum_q psi_m(q) Q(q)
-            const int r = it - n_lines;
-            const int s = r / NP, m = r % NP;
-            T acc = 0;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) acc += ((DIM == 3) ? ct.PSI3[q * 8 + m] : ct.PSI2[q * 4 + m]) * sX[s * Cfg::SX + q];
-            sOp[s * NP + m] = acc;
+            for (int q = 0; q < NQ; ++q) acc[q] = 0;
           }
-        }
-        __syncthreads();
-      }
-      // ---- transposed value passes -> nodal output in sO
-      for (int dir = 0; dir < DIM; ++dir) {
-        for (int it = threadIdx.x; it < ns * NC * NL; it += blockDim.x) {
-          const int s = it / (NC * NL), r = it % (NC * NL);
-          const int c = r / NL, l = r % NL;
-          T* gsl = sG + s * Cfg::SG + (c * DIM + DIM - 1) * NQ;
-          T* dst = (dir == DIM - 1) ? sO + s * Cfg::SX + c * NQ : gsl;
-          line_pass<DIM, T>(gsl, dir, l, ct.Bt, dst);
-        }
-        __syncthreads();
-      }
-      if constexpr (MODE == OP_RES) {
-        // ---- value terms in nodal form: M_e (-sum_j K_ij u_j + m_i v^- + tau w_i f_i)
-        const T* vp = reinterpret_cast<const T*>(a.vprev);
-        const T* ff = reinterpret_cast<const T*>(a.f);
-        for (int it = threadIdx.x; it < nc * NC * NQ; it += blockDim.x) {
-          const int ci = it / (NC * NQ), c = (it / NQ) % NC, q = it % NQ;
+          const T* gs = sG + s * Cfg::SG + c * DIM * NQ;
+          rpass_acc<DIM, 0>(acc, sDdt[0], gs);
+          rpass_acc<DIM, 1>(acc, sDdt[1], gs + NQ);
+          if constexpr (DIM == 3) rpass_acc<DIM, 2>(acc, sDdt[2], gs + 2 * NQ);
+          rpass<DIM, 0>(acc, ct.Bt);
+          rpass<DIM, 1>(acc, ct.Bt);
+          if constexpr (DIM == 3) rpass<DIM, 2>(acc, ct.Bt);
           const int cell = sCell[ci];
           const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
-          const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-          const long gn = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz)) + c * a.Nq2;
-          T uj[K1];
+          if constexpr (MODE == OP_RES) {
+            // value terms in nodal form: M_e (-sum_j K_ij u_j + m_i v^- + tau w_i f_i)
+            const T* vp = reinterpret_cast<const T*>(a.vprev);
+            const T* ff = reinterpret_cast<const T*>(a.f);
+            T y[NQ];
 #pragma unroll
-          for (int j = 0; j < K1; ++j) uj[j] = in[(long)j * a.Mv + gn];
-          const T v = vp ? vp[gn] : (T)0;
+            for (int q = 0; q < NQ; ++q) {
+              const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
+              const long gn = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz)) + c * a.Nq2;
+              T t = vp ? (T)a.mt[mu] * vp[gn] : (T)0;
 #pragma unroll
-          for (int i = 0; i < K1; ++i) {
-            T y = (T)a.mt[i] * v;
-#pragma unroll
-            for (int j = 0; j < K1; ++j) y -= (T)a.Kt[i * K1 + j] * uj[j];
-            if (ff) y += (T)a.tw[i] * ff[(long)i * a.Mv + gn];
-            sX[(ci * K1 + i) * Cfg::SX + c * NQ + q] = y;
-          }
-        }
-        __syncthreads();
-        for (int dir = 0; dir < DIM; ++dir) {
-          for (int it = threadIdx.x; it < ns * NC * NL; it += blockDim.x) {
-            const int s = it / (NC * NL), r = it % (NC * NL);
-            T* x = sX + s * Cfg::SX + (r / NL) * NQ;
-            line_pass<DIM, T>(x, dir, r % NL, sM1[dir], x);
-          }
-          __syncthreads();
-        }
-        for (int it = threadIdx.x; it < ns * NC * NQ; it += blockDim.x) {
-          const int s = it / (NC * NQ), r = it % (NC * NQ);
-          sO[s * Cfg::SX + r] += sX[s * Cfg::SX + r];
-        }
-        __syncthreads();
-      }
-    }
-
-    // ---- boundary faces, in rounds of at most one face per slot
-    const int nrounds = sBfaces;
-    for (int round = 0; round < nrounds; ++round) {
-      if (threadIdx.x == 0) {
-        int na = 0;
-        for (int s = 0; s < ns; ++s) {
-          const int ci = s / K1;
-          const int cell = sCell[ci];
-          const int e3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1], (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0};
-          int r = 0, side = -1;
-          for (int sd = 0; sd < 2 * DIM && side < 0; ++sd) {
-            const int ax = sd >> 1, up = sd & 1;
-            const bool on = up ? (e3[ax] == a.n[ax] - 1) : (e3[ax] == 0);
-            if (on) {
-              if (r == round) side = sd;
-              ++r;
+              for (int j = 0; j < K1; ++j) t -= (T)a.Kt[mu * K1 + j] * in[(long)j * a.Mv + gn];
+              if (ff) t += (T)a.tw[mu] * ff[(long)mu * a.Mv + gn];
+              y[q] = t;
             }
+            rpass<DIM, 0>(y, sM1[0]);
+            rpass<DIM, 1>(y, sM1[1]);
+            if constexpr (DIM == 3) rpass<DIM, 2>(y, sM1[2]);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[q] += y[q];
           }
-          sFside[s] = side;
-          if (side >= 0) {
-            sAct[na++] = s;
-            sFid[s] = a.face_off[a.col_start + b0 + ci] + round;
+          // scatter-add (cells of one colour class share no node): all loads
+          // first so that they are in flight together, then the stores
+          T* ob = out + (long)mu * a.Mv + c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
+            acc[q] += ob[qx + a.g2[0] * (qy + a.g2[1] * qz)];
           }
-        }
-        sNact = na;
-      }
-      __syncthreads();
-      const int na = sNact;
-      // workspace inside the slot's gradient array: PV[NC][NFQ], PN[NC][NFQ], PT[NC][DIM-1][NFQ], FQ[NFQ]
-      constexpr int oPV = 0, oPN = NC * NFQ, oPT = 2 * NC * NFQ, oFQ = 2 * NC * NFQ + NC * (DIM - 1) * NFQ;
-      // FA: face-plane nodal values and normal derivatives
-      for (int it = threadIdx.x; it < na * NC * NFQ; it += blockDim.x) {
-        const int ai = it / (NC * NFQ), c = (it / NFQ) % NC, tn = it % NFQ;
-        const int s = sAct[ai], side = sFside[s], ax = side >> 1, up = side & 1;
-        const int ci = s / K1, mu = s % K1;
-        const int cell = sCell[ci];
-        const int e3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1], (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0};
-        const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-        int pos[3] = {0, 0, 0};
-        pos[t1] = tn % 3;
-        if (DIM == 3) pos[t2] = tn / 3;
-        T v[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          pos[ax] = i;
-          const long gnode = (2L * e3[0] + pos[0]) + a.g2[0] * ((2L * e3[1] + pos[1]) + a.g2[1] * (2L * e3[2] + pos[2]));
-          v[i] = in[(long)mu * a.Mv + c * a.Nq2 + gnode];
-        }
-        T* w = sG + s * Cfg::SG;
-        w[oPV + c * NFQ + tn] = up ? v[2] : v[0];
-        const T ih = (T)a.ih[ax];
-        w[oPN + c * NFQ + tn] = ((T)ct.ED[up * 3 + 0] * v[0] + (T)ct.ED[up * 3 + 1] * v[1] + (T)ct.ED[up * 3 + 2] * v[2]) * ih;
-      }
-      __syncthreads();
-      // FB: values at the face points (tangential passes on PV and PN)
-      for (int td = 0; td < DIM - 1; ++td) {
-        constexpr int FL = (DIM == 3) ? 3 : 1;
-        for (int it = threadIdx.x; it < na * NC * 2 * FL; it += blockDim.x) {
-          const int ai = it / (NC * 2 * FL), c = (it / (2 * FL)) % NC, wh = (it / FL) % 2, l = it % FL;
-          const int s = sAct[ai];
-          T* x = sG + s * Cfg::SG + (wh ? oPN : oPV) + c * NFQ;
-          // face plane indexed tn = i1 + 3 i2: lines along i1 (td = 0) or i2 (td = 1)
-          const int b = (td == 0) ? 3 * l : l, st = (td == 0) ? 1 : 3;
-          T y0, y1, y2;
-          apply3<T, T>(ct.B, x[b], x[b + st], x[b + 2 * st], y0, y1, y2);
-          x[b] = y0;
-          x[b + st] = y1;
-          x[b + 2 * st] = y2;
-        }
-        __syncthreads();
-      }
-      // FC: tangential derivatives at the face points (collocation form)
-      {
-        constexpr int FL = (DIM == 3) ? 3 : 1;
-        for (int it = threadIdx.x; it < na * NC * (DIM - 1) * FL; it += blockDim.x) {
-          const int ai = it / (NC * (DIM - 1) * FL), c = (it / ((DIM - 1) * FL)) % NC, td = (it / FL) % (DIM - 1),
-                    l = it % FL;
-          const int s = sAct[ai], side = sFside[s], ax = side >> 1;
-          const int tax = (td == 0) ? (ax == 0 ? 1 : 0) : (ax == 2 ? 1 : 2);
-          const T* x = sG + s * Cfg::SG + oPV + c * NFQ;
-          T* y = sG + s * Cfg::SG + oPT + (c * (DIM - 1) + td) * NFQ;
-          const int b = (td == 0) ? 3 * l : l, st = (td == 0) ? 1 : 3;
-          T y0, y1, y2;
-          apply3<T, T>(Dd[tax], x[b], x[b + st], x[b + 2 * st], y0, y1, y2);
-          y[b] = y0;
-          y[b + st] = y1;
-          y[b + 2 * st] = y2;
-        }
-        __syncthreads();
-      }
-      // FD: pointwise face terms
-      for (int it = threadIdx.x; it < na * NFQ; it += blockDim.x) {
-        const int ai = it / NFQ, fq = it % NFQ;
-        const int s = sAct[ai], side = sFside[s], ax = side >> 1, up = side & 1;
-        const int ci = s / K1, mu = s % K1;
-        const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-        const bool isD = (a.dmask >> side) & 1u;
-        T* w = sG + s * Cfg::SG;
-        T u[3] = {0, 0, 0}, g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          u[c] = w[oPV + c * NFQ + fq];
-          g[c][ax] = w[oPN + c * NFQ + fq];
-          g[c][t1] = w[oPT + (c * (DIM - 1) + 0) * NFQ + fq];
-          if (DIM == 3) g[c][t2] = w[oPT + (c * (DIM - 1) + 1) * NFQ + fq];
-        }
-        const T nsg = up ? (T)1 : (T)-1;  // n = nsg e_ax
-        // pressure at the face point from the face's Q1 nodes
-        T pf = 0;
-        {
-#pragma unroll
-          for (int m = 0; m < D::NFP; ++m) {
-            int mm[3] = {0, 0, 0};
-            mm[ax] = up;
-            mm[t1] = m & 1;
-            if (DIM == 3) mm[t2] = m >> 1;
-            const int pm = mm[0] + 2 * mm[1] + 4 * mm[2];
-            pf += ((DIM == 3) ? ct.FPSI3[fq * 4 + m] : ct.FPSI2[fq * 2 + m]) * sP[s * NP + pm];
+          for (int q = 0; q < NQ; ++q) {
+            const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
+            ob[qx + a.g2[0] * (qy + a.g2[1] * qz)] = acc[q];
           }
-        }
-        const double hD = a.h[ax];
-        T V[3] = {0, 0, 0}, Gf[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Qf = 0;
-        if constexpr (MODE == OP_LIN) {
-          // physical point, face weight
-          const int cell = sCell[ci];
-          const int e3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1], (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0};
-          const double* Wg = cT.W;
-          const double gpt[3] = {0.5 - 0.3872983346207417, 0.5, 0.5 + 0.3872983346207417};
-          double r3[3] = {0, 0, 0};
-          r3[ax] = up ? 1.0 : 0.0;
-          r3[t1] = gpt[fq % 3];
-          if (DIM == 3) r3[t2] = gpt[fq / 3];
-          double x[3];
-          for (int d = 0; d < 3; ++d) x[d] = d < DIM ? (e3[d] + r3[d]) * a.h[d] : 0.0;
-          double fw = ((DIM == 3) ? cT.FW3[fq] : cT.FW2[fq]) * a.tw[mu];
-          for (int d = 0; d < DIM; ++d)
-            if (d != ax) fw *= a.h[d];
-          (void)Wg;
-          double Am[NS];
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) Am[i] = (double)g[i][i];
-          Am[DIM] = 0.5 * ((double)g[0][1] + (double)g[1][0]);
-          if (DIM == 3) {
-            Am[4] = 0.5 * ((double)g[0][2] + (double)g[2][0]);
-            Am[5] = 0.5 * ((double)g[1][2] + (double)g[2][1]);
-          }
-          double a2 = 0.0;
-#pragma unroll
-          for (int i = 0; i < NS; ++i) a2 += (i < DIM ? 1.0 : 2.0) * Am[i] * Am[i];
-          const double D2 = a.delta * a.delta + a2;
-          const double mu_m = a.nu * pow(D2, 0.5 * (a.p - 2.0));
-          const double eta = a.nu_inf + mu_m;
-          double cfac = 0.0;
-          if (a.tangent == ST_EXN) {
-            cfac = (a.p - 2.0) * mu_m / D2;
-          } else if (a.tangent == ST_MODN) {
-            const double sig = mu_m * sqrt(a2);
-            const double sc = sig > 0.0 ? fmin(1.0, a.sigma_max / sig) : 0.0;
-            cfac = sc * (a.p - 2.0) * mu_m / D2;
-          }
-          const double un = (double)nsg * (double)u[ax];
-          const double negp = 0.5 * (fabs(un) - un);
-          double gl[3], ggr[9];
-          lifting(a, x, gl, ggr);
-          double Dg[NS];
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) Dg[i] = ggr[i * 3 + i];
-          Dg[DIM] = 0.5 * (ggr[1] + ggr[3]);
-          if (DIM == 3) {
-            Dg[4] = 0.5 * (ggr[2] + ggr[6]);
-            Dg[5] = 0.5 * (ggr[5] + ggr[7]);
-          }
-          double g2n = 0.0;
-#pragma unroll
-          for (int i = 0; i < NS; ++i) g2n += (i < DIM ? 1.0 : 2.0) * Dg[i] * Dg[i];
-          const double DgD = a.delta * a.delta + g2n;
-          const double etaD = a.nu_inf + a.nu * pow(DgD, 0.5 * (a.p - 2.0));
-          const double betaD = a.nu * (a.p - 2.0) * pow(DgD, 0.5 * (a.p - 4.0));
-          const long fid = sFid[s];
-          double* cp = a.wfcache + ((fid * K1 + mu) * (long)D::NF_FACE) * NFQ + fq;
-          int o = 0;
-          cp[(o++) * NFQ] = eta * fw;
-          cp[(o++) * NFQ] = cfac * fw;
-#pragma unroll
-          for (int i = 0; i < NS; ++i) cp[(o++) * NFQ] = Am[i];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) cp[(o++) * NFQ] = (double)u[c] * fw;
-          cp[(o++) * NFQ] = negp * fw;
-          cp[(o++) * NFQ] = a.gamma1 / hD * etaD * fw;
-          cp[(o++) * NFQ] = a.gamma2 / hD * fw;
-          cp[(o++) * NFQ] = etaD * fw;
-          cp[(o++) * NFQ] = betaD * fw;
-#pragma unroll
-          for (int i = 0; i < NS; ++i) cp[(o++) * NFQ] = Dg[i];
-          cp[(o++) * NFQ] = fw;
-          (void)pf;
-          (void)isD;
-          continue;
-        } else if constexpr (MODE == OP_JAC) {
-          const T* cp = reinterpret_cast<const T*>(a.fcache) + (((long)sFid[s] * K1 + mu) * (long)D::NF_FACE) * NFQ + fq;
-          constexpr int oU = 2 + NS, oN = oU + NC;
-          T uw[3] = {0, 0, 0};
-#pragma unroll
-          for (int c = 0; c < NC; ++c) uw[c] = cp[(oU + c) * NFQ];
-          const T unw = nsg * uw[ax];
-          const T dun = nsg * u[ax];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) V[c] = unw * u[c] + (TAN == 1 ? dun * uw[c] : (T)0);
-          if (isD) {
-            const T etaw = cp[0], cw = cp[NQ > 0 ? NFQ : 0];
-            T Am[NS];
-#pragma unroll
-            for (int i = 0; i < NS; ++i) Am[i] = cp[(2 + i) * NFQ];
-            const T negw = cp[oN * NFQ], pen1 = cp[(oN + 1) * NFQ], pen2 = cp[(oN + 2) * NFQ];
-            const T etaDw = cp[(oN + 3) * NFQ], betaDw = cp[(oN + 4) * NFQ];
-            T Dg[NS];
-#pragma unroll
-            for (int i = 0; i < NS; ++i) Dg[i] = cp[(oN + 5 + i) * NFQ];
-            const T fw = cp[(oN + 5 + NS) * NFQ];
-            // B = D(du) (full), (T B) n
-            T Bm[3][3];
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j) Bm[i][j] = (T)0.5 * (g[i][j] + g[j][i]);
-            T AB = 0;
-            if (TAN == 1) {
-#pragma unroll
-              for (int i = 0; i < DIM; ++i)
-#pragma unroll
-                for (int j = 0; j < DIM; ++j) AB += Am[sym_idx<DIM>(i, j)] * Bm[i][j];
-            }
-            const T sfac = cw * AB;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              const T Tn = nsg * (etaw * Bm[c][ax] + (TAN == 1 ? sfac * Am[sym_idx<DIM>(c, ax)] : (T)0));
-              V[c] += -Tn - negw * u[c] + pen1 * u[c];
-            }
-            V[ax] += nsg * (pf * fw) + pen2 * dun * nsg;
-            // -(du, DS(Dg)(Dz) n) = -DS(Dg)(sym(du (x) n)) : grad z
-            T Sd[3][3];
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j)
-                Sd[i][j] = (T)0.5 * ((j == ax ? nsg * u[i] : (T)0) + (i == ax ? nsg * u[j] : (T)0));
-            T gS = 0;
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j) gS += Dg[sym_idx<DIM>(i, j)] * Sd[i][j];
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j) Gf[i][j] = -(etaDw * Sd[i][j] + betaDw * gS * Dg[sym_idx<DIM>(i, j)]);
-            Qf = (T)a.q_sign * dun * fw;
-          }
-        } else {  // OP_RES face terms, F = RHS - LHS
-          const int cell = sCell[ci];
-          const int e3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1], (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0};
-          const double gpt[3] = {0.5 - 0.3872983346207417, 0.5, 0.5 + 0.3872983346207417};
-          double r3[3] = {0, 0, 0};
-          r3[ax] = up ? 1.0 : 0.0;
-          r3[t1] = gpt[fq % 3];
-          if (DIM == 3) r3[t2] = gpt[fq / 3];
-          double x[3];
-          for (int d = 0; d < 3; ++d) x[d] = d < DIM ? (e3[d] + r3[d]) * a.h[d] : 0.0;
-          double fwd = ((DIM == 3) ? cT.FW3[fq] : cT.FW2[fq]) * a.tw[mu];
-          for (int d = 0; d < DIM; ++d)
-            if (d != ax) fwd *= a.h[d];
-          const T fw = (T)fwd;
-          const T un = nsg * u[ax];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) V[c] = -un * u[c] * fw;
-          if (isD) {
-            double gl[3], ggr[9];
-            lifting(a, x, gl, ggr);
-            double Dgf[3][3];
-            double g2n = 0.0;
-            for (int i = 0; i < 3; ++i)
-              for (int j = 0; j < 3; ++j) {
-                Dgf[i][j] = 0.5 * (ggr[i * 3 + j] + ggr[j * 3 + i]);
-                g2n += Dgf[i][j] * Dgf[i][j];
-              }
-            const double DgD = a.delta * a.delta + g2n;
-            const T etaD = (T)(a.nu_inf + a.nu * pow(DgD, 0.5 * (a.p - 2.0)));
-            const T betaD = (T)(a.nu * (a.p - 2.0) * pow(DgD, 0.5 * (a.p - 4.0)));
-            T A[3][3];
-            T a2 = 0;
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j) {
-                A[i][j] = (T)0.5 * (g[i][j] + g[j][i]);
-                a2 += A[i][j] * A[i][j];
-              }
-            const T eta = (T)a.nu_inf + (T)a.nu * pow((T)(a.delta * a.delta) + a2, (T)(0.5 * (a.p - 2.0)));
-            const T gn = nsg * (T)gl[ax];
-            const T negu = (T)0.5 * (fabs(un) - un), negg = (T)0.5 * (fabs(gn) - gn);
-            T dlt[3] = {0, 0, 0};
-#pragma unroll
-            for (int c = 0; c < NC; ++c) dlt[c] = u[c] - (T)gl[c];
-            const T dn = nsg * dlt[ax];
-            const T p1 = (T)(a.gamma1 / hD) * etaD, p2 = (T)(a.gamma2 / hD);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              const T Sn = nsg * eta * A[c][ax];
-              V[c] += (Sn - (c == ax ? nsg * pf : (T)0) + negu * u[c] - negg * (T)gl[c] - p1 * dlt[c] -
-                       (c == ax ? p2 * dn * nsg : (T)0)) * fw;
-            }
-            T Sd[3][3];
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j)
-                Sd[i][j] = (T)0.5 * ((j == ax ? nsg * dlt[i] : (T)0) + (i == ax ? nsg * dlt[j] : (T)0));
-            T gS = 0;
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j) gS += (T)Dgf[i][j] * Sd[i][j];
-#pragma unroll
-            for (int i = 0; i < DIM; ++i)
-#pragma unroll
-              for (int j = 0; j < DIM; ++j) Gf[i][j] = (etaD * Sd[i][j] + betaD * gS * (T)Dgf[i][j]) * fw;
-            Qf = -(T)a.q_sign * dn * fw;
-          }
-        }
-        if constexpr (MODE != OP_LIN) {
-          // store fluxes in place: FV <- PV slot, FGn <- PN slot, FGt <- PT slot
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            w[oPV + c * NFQ + fq] = V[c];
-            w[oPN + c * NFQ + fq] = Gf[c][ax];
-            w[oPT + (c * (DIM - 1) + 0) * NFQ + fq] = Gf[c][t1];
-            if (DIM == 3) w[oPT + (c * (DIM - 1) + 1) * NFQ + fq] = Gf[c][t2];
-          }
-          w[oFQ + fq] = Qf;
-        }
-      }
-      __syncthreads();
-      if constexpr (MODE != OP_LIN) {
-        constexpr int FL = (DIM == 3) ? 3 : 1;
-        // FE1: tangential derivative tests, chained into FV
-        for (int td = 0; td < DIM - 1; ++td) {
-          for (int it = threadIdx.x; it < na * NC * FL; it += blockDim.x) {
-            const int ai = it / (NC * FL), c = (it / FL) % NC, l = it % FL;
-            const int s = sAct[ai], side = sFside[s], ax = side >> 1;
-            const int tax = (td == 0) ? (ax == 0 ? 1 : 0) : (ax == 2 ? 1 : 2);
-            T* w = sG + s * Cfg::SG;
-            const T* x = w + oPT + (c * (DIM - 1) + td) * NFQ;
-            T* y = w + oPV + c * NFQ;
-            const int b = (td == 0) ? 3 * l : l, st = (td == 0) ? 1 : 3;
-            const T* m = Ddt[tax];
-            const T x0 = x[b], x1 = x[b + st], x2 = x[b + 2 * st];
-            y[b] += m[0] * x0 + m[1] * x1 + m[2] * x2;
-            y[b + st] += m[3] * x0 + m[4] * x1 + m[5] * x2;
-            y[b + 2 * st] += m[6] * x0 + m[7] * x1 + m[8] * x2;
-          }
-          __syncthreads();
-        }
-        // FE2: transposed tangential value passes on FV and FGn
-        for (int td = 0; td < DIM - 1; ++td) {
-          for (int it = threadIdx.x; it < na * NC * 2 * FL; it += blockDim.x) {
-            const int ai = it / (NC * 2 * FL), c = (it / (2 * FL)) % NC, wh = (it / FL) % 2, l = it % FL;
-            const int s = sAct[ai];
-            T* x = sG + s * Cfg::SG + (wh ? oPN : oPV) + c * NFQ;
-            const int b = (td == 0) ? 3 * l : l, st = (td == 0) ? 1 : 3;
-            T y0, y1, y2;
-            apply3<T, T>(ct.Bt, x[b], x[b + st], x[b + 2 * st], y0, y1, y2);
-            x[b] = y0;
-            x[b + st] = y1;
-            x[b + 2 * st] = y2;
-          }
-          __syncthreads();
-        }
-        // FF: expand onto the cell's nodes along the normal; pressure test
-        for (int it = threadIdx.x; it < na * (NC * NFQ + D::NFP); it += blockDim.x) {
-          const int ai = it / (NC * NFQ + D::NFP), r = it % (NC * NFQ + D::NFP);
-          const int s = sAct[ai], side = sFside[s], ax = side >> 1, up = side & 1;
-          const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-          T* w = sG + s * Cfg::SG;
-          if (r < NC * NFQ) {
-            const int c = r / NFQ, tn = r % NFQ;
-            int pos[3] = {0, 0, 0};
-            pos[t1] = tn % 3;
-            if (DIM == 3) pos[t2] = tn / 3;
-            const T fv = w[oPV + c * NFQ + tn], fn = w[oPN + c * NFQ + tn] * (T)a.ih[ax];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              pos[ax] = i;
-              const int q = pos[0] + 3 * pos[1] + 9 * pos[2];
-              sO[s * Cfg::SX + c * NQ + q] += (T)ct.E[up * 3 + i] * fv + (T)ct.ED[up * 3 + i] * fn;
-            }
-          } else {
-            const int m = r - NC * NFQ;
-            int mm[3] = {0, 0, 0};
-            mm[ax] = up;
-            mm[t1] = m & 1;
-            if (DIM == 3) mm[t2] = m >> 1;
-            const int pm = mm[0] + 2 * mm[1] + 4 * mm[2];
-            T acc = 0;
-#pragma unroll
-            for (int fq = 0; fq < NFQ; ++fq)
-              acc += ((DIM == 3) ? ct.FPSI3[fq * 4 + m] : ct.FPSI2[fq * 2 + m]) * w[oFQ + fq];
-            sOp[s * NP + pm] += acc;
-          }
-        }
-        __syncthreads();
-      }
-    }
-
-    // ---- scatter-add (cells of one colour class share no node)
-    if constexpr (MODE != OP_LIN) {
-      for (int it = threadIdx.x; it < ns * (NC * NQ + NP); it += blockDim.x) {
-        const int s = it / (NC * NQ + NP), r = it % (NC * NQ + NP);
-        const int ci = s / K1, mu = s % K1;
-        const int cell = sCell[ci];
-        const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
-        if (r < NC * NQ) {
-          const int c = r / NQ, q = r % NQ;
-          const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-          const long g = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz));
-          const long gi = (long)mu * a.Mv + c * a.Nq2 + g;
-          out[gi] += sO[s * Cfg::SX + r];
         } else {
-          const int m = r - NC * NQ;
+          const int r = it - ns * NC;
+          const int s = r / NP, m = r % NP;
+          const int ci = s / K1, mu = s % K1;
+          T acc = 0;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) acc += ((DIM == 3) ? ct.PSI3[q * 8 + m] : ct.PSI2[q * 4 + m]) * sQ[s * NQ + q];
+          const int cell = sCell[ci];
+          const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
           const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
           const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
-          out[(long)K1 * a.Mv + (long)mu * a.Mp + g] += sOp[s * NP + m];
+          out[(long)K1 * a.Mv + (long)mu * a.Mp + g] += acc;
         }
       }
     }
