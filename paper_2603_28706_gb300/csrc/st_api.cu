@@ -6,6 +6,7 @@
 
 #include "st_blas.cuh"
 #include "st_internal.h"
+#include "st_face.cuh"
 #include "st_operator.cuh"
 
 namespace st {
@@ -130,6 +131,73 @@ std::vector<int> face_lists(const st_params& P, Level& L, std::vector<int>& fcel
   off[L.ncells] = (int)fcell.size();
   L.nfaces = (long)fcell.size();
   return off;
+}
+
+// Per node of the boundary-cell layer: the (face, face-node) pairs that reach
+// it, with the normal-direction weights of the Q2 basis (velocity nodes) or
+// the face pressure node (pressure nodes).
+cudaError_t build_gather(const st_problem* h, Level& L, const std::vector<int>& off) {
+  const int d = h->dim;
+  std::vector<std::vector<GatherEnt>> vel(L.Nq2), pres(L.Nq1);
+  for (long cell = 0; cell < L.ncells; ++cell) {
+    const int e3[3] = {(int)(cell % L.n[0]), (int)((cell / L.n[0]) % L.n[1]), (int)(cell / ((long)L.n[0] * L.n[1]))};
+    int rank = 0;
+    for (int sd = 0; sd < 2 * d; ++sd) {
+      const int ax = sd >> 1, up = sd & 1;
+      const bool on = up ? (e3[ax] == L.n[ax] - 1) : (e3[ax] == 0);
+      if (!on) continue;
+      const int fid = off[cell] + rank++;
+      const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+      for (int z = 0; z < (d == 3 ? 3 : 1); ++z)
+        for (int y = 0; y < 3; ++y)
+          for (int x = 0; x < 3; ++x) {
+            const int l3[3] = {x, y, z};
+            const long gn = (2L * e3[0] + x) + L.g2[0] * ((2L * e3[1] + y) + L.g2[1] * (2L * e3[2] + z));
+            GatherEnt g;
+            g.fid = fid;
+            g.tn = l3[t1] + 3 * (d == 3 ? l3[t2] : 0);
+            g.e = h->R.E[up * 3 + l3[ax]];
+            g.ed = h->R.ED[up * 3 + l3[ax]];
+            vel[gn].push_back(g);
+          }
+      for (int z = 0; z < (d == 3 ? 2 : 1); ++z)
+        for (int y = 0; y < 2; ++y)
+          for (int x = 0; x < 2; ++x) {
+            const int m3[3] = {x, y, z};
+            if (m3[ax] != up) continue;
+            const long gp = (e3[0] + x) + L.g1[0] * ((e3[1] + y) + L.g1[1] * (e3[2] + z));
+            GatherEnt g;
+            g.fid = fid;
+            g.tn = m3[t1] + 2 * (d == 3 ? m3[t2] : 0);
+            g.e = g.ed = 0.0;
+            pres[gp].push_back(g);
+          }
+    }
+  }
+  std::vector<int> node, ptr(1, 0);
+  std::vector<GatherEnt> ent;
+  for (long i = 0; i < L.Nq2; ++i)
+    if (!vel[i].empty()) {
+      node.push_back((int)i);
+      ent.insert(ent.end(), vel[i].begin(), vel[i].end());
+      ptr.push_back((int)ent.size());
+    }
+  L.n_gather_vel = (int)node.size();
+  for (long i = 0; i < L.Nq1; ++i)
+    if (!pres[i].empty()) {
+      node.push_back((int)i);
+      ent.insert(ent.end(), pres[i].begin(), pres[i].end());
+      ptr.push_back((int)ent.size());
+    }
+  L.n_gather = (int)node.size();
+  if (node.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&L.d_gnode, node.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(L.d_gnode, node.data(), node.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&L.d_gptr, ptr.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(L.d_gptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&L.d_gent, ent.size() * sizeof(GatherEnt));
+  if (e == cudaSuccess) e = cudaMemcpy(L.d_gent, ent.data(), ent.size() * sizeof(GatherEnt), cudaMemcpyHostToDevice);
+  return e;
 }
 
 st_status check_params(const st_params& P, std::string& why) {
@@ -286,6 +354,7 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
       e = cudaMemcpy(Lv.d_face_cell, fcell.data(), fcell.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&Lv.d_face_side, fside.size());
     if (e == cudaSuccess) e = cudaMemcpy(Lv.d_face_side, fside.data(), fside.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = build_gather(h, Lv, off);
     if (e != cudaSuccess) {
       st_destroy(h);
       return e == cudaErrorMemoryAllocation ? ST_ENOMEM : ST_ECUDA;
@@ -329,6 +398,9 @@ st_status st_destroy(st_problem* h) {
     cudaFree(L.d_face_off);
     cudaFree(L.d_face_cell);
     cudaFree(L.d_face_side);
+    cudaFree(L.d_gnode);
+    cudaFree(L.d_gptr);
+    cudaFree(L.d_gent);
   }
   cudaFree(h->d_cache64);
   cudaFree(h->d_fcache64);

@@ -431,96 +431,57 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
   }
 }
 
-// Adds the boundary-face contributions into out, one thread per global node:
-// the node's value collects, from every boundary face of every cell that
-// contains it, E_i * FV + ED_i * FGn (velocity) or the face pressure test.
-// Each node is written by exactly one thread (no atomics, deterministic).
+// Adds the boundary-face contributions into out, one thread per node of the
+// boundary-cell layer.  The host lists, per such node, every (face, face-node)
+// pair that reaches it with the weights E_i and ED_i of the Q2 basis along the
+// face normal (velocity) or the face pressure-test index (pressure).  Each
+// node is written by exactly one thread (no atomics, deterministic).
+struct GatherEnt {
+  int fid;    // boundary face
+  int tn;     // face-plane node (velocity) or face pressure node (pressure)
+  double e;   // weight of the face value output
+  double ed;  // weight of the face normal-derivative output
+};
+
 template <int DIM, int K1, typename T>
-__global__ void st_face_gather(const OpArgs a, const int* __restrict__ face_off_lin, const T* __restrict__ fscr,
+__global__ void st_face_gather(const OpArgs a, int nvel, const int* __restrict__ gnode, const int* __restrict__ gptr,
+                               const GatherEnt* __restrict__ gent, int ntot, const T* __restrict__ fscr,
                                T* __restrict__ out) {
   using D = Dims<DIM>;
   constexpr int NC = D::NC, NFQ = D::NFQ, NFP = D::NFP;
   constexpr int NOUT = 2 * NC * NFQ + NFP;
-  const auto& ct = CT<T>::t();
-  const long nv = a.Nq2, np = a.Nq1;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nv + np; t += (long)gridDim.x * blockDim.x) {
-    const bool vel = t < nv;
-    const long node = vel ? t : t - nv;
-    const long* g = vel ? a.g2 : a.g1;
-    const int ix = (int)(node % g[0]), iy = (int)((node / g[0]) % g[1]), iz = (int)(node / (g[0] * g[1]));
-    const int idx3[3] = {ix, iy, iz};
-    // quick exit: the node lies in no boundary cell
-    bool near = false;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += gridDim.x * blockDim.x) {
+    const int node = gnode[t];
+    const int b = gptr[t], e = gptr[t + 1];
+    if (t < nvel) {
+      T acc[K1 * NC];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const int lim = vel ? 2 : 1;
-      near |= idx3[d] <= lim || idx3[d] >= (int)g[d] - 1 - lim;
-    }
-    if (!near) continue;
-    // candidate cells per direction (at most two) and the local index in each
-    int ce[3][2], cl[3][2], cn[3];
+      for (int i = 0; i < K1 * NC; ++i) acc[i] = 0;
+      for (int j = b; j < e; ++j) {
+        const GatherEnt g = gent[j];
+        const T ev = (T)g.e, ed = (T)g.ed;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      cn[d] = 0;
-      if (d >= DIM) {
-        ce[d][0] = 0;
-        cl[d][0] = 0;
-        cn[d] = 1;
-        continue;
-      }
-      const int i = idx3[d];
-      if (vel) {
-        if (i & 1) {
-          ce[d][0] = (i - 1) / 2;
-          cl[d][0] = 1;
-          cn[d] = 1;
-        } else {
-          if (i / 2 - 1 >= 0) { ce[d][cn[d]] = i / 2 - 1; cl[d][cn[d]] = 2; ++cn[d]; }
-          if (i / 2 < a.n[d]) { ce[d][cn[d]] = i / 2; cl[d][cn[d]] = 0; ++cn[d]; }
+        for (int mu = 0; mu < K1; ++mu) {
+          const T* fs = fscr + ((long)g.fid * K1 + mu) * NOUT + g.tn;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[mu * NC + c] += ev * fs[c * NFQ] + ed * fs[NC * NFQ + c * NFQ];
         }
-      } else {
-        if (i - 1 >= 0) { ce[d][cn[d]] = i - 1; cl[d][cn[d]] = 1; ++cn[d]; }
-        if (i < a.n[d]) { ce[d][cn[d]] = i; cl[d][cn[d]] = 0; ++cn[d]; }
       }
-    }
-    T acc[K1 * 3];
 #pragma unroll
-    for (int i = 0; i < K1 * 3; ++i) acc[i] = 0;
-    for (int cz = 0; cz < cn[2]; ++cz)
-      for (int cy = 0; cy < cn[1]; ++cy)
-        for (int cx = 0; cx < cn[0]; ++cx) {
-          const int e3[3] = {ce[0][cx], ce[1][cy], ce[2][cz]};
-          const int l3[3] = {cl[0][cx], cl[1][cy], cl[2][cz]};
-          const int cell = e3[0] + a.n[0] * (e3[1] + a.n[1] * e3[2]);
-          int rank = 0;
-          for (int sd = 0; sd < 2 * DIM; ++sd) {
-            const int ax = sd >> 1, up = sd & 1;
-            const bool on = up ? (e3[ax] == a.n[ax] - 1) : (e3[ax] == 0);
-            if (!on) continue;
-            const int fid = face_off_lin[cell] + rank;
-            ++rank;
-            const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-            const int lt1 = l3[t1], lt2 = (DIM == 3) ? l3[t2] : 0;
-            if (vel) {
-              const int i = l3[ax];
-              const T e = (T)ct.E[up * 3 + i], ed = (T)ct.ED[up * 3 + i];
-              const int tn = lt1 + 3 * lt2;
-              for (int mu = 0; mu < K1; ++mu) {
-                const T* fs = fscr + ((long)fid * K1 + mu) * NOUT;
-                for (int c = 0; c < NC; ++c) acc[mu * 3 + c] += e * fs[c * NFQ + tn] + ed * fs[NC * NFQ + c * NFQ + tn];
-              }
-            } else {
-              if (l3[ax] != up) continue;  // pressure node not on this face
-              const int m = lt1 + 2 * lt2;
-              for (int mu = 0; mu < K1; ++mu) acc[mu * 3] += fscr[((long)fid * K1 + mu) * NOUT + 2 * NC * NFQ + m];
-            }
-          }
-        }
-    if (vel) {
       for (int mu = 0; mu < K1; ++mu)
-        for (int c = 0; c < NC; ++c) out[(long)mu * a.Mv + c * a.Nq2 + node] += acc[mu * 3 + c];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[(long)mu * a.Mv + (long)c * a.Nq2 + node] += acc[mu * NC + c];
     } else {
-      for (int mu = 0; mu < K1; ++mu) out[(long)K1 * a.Mv + (long)mu * a.Mp + node] += acc[mu * 3];
+      T acc[K1];
+#pragma unroll
+      for (int i = 0; i < K1; ++i) acc[i] = 0;
+      for (int j = b; j < e; ++j) {
+        const GatherEnt g = gent[j];
+#pragma unroll
+        for (int mu = 0; mu < K1; ++mu) acc[mu] += fscr[((long)g.fid * K1 + mu) * NOUT + 2 * NC * NFQ + g.tn];
+      }
+#pragma unroll
+      for (int mu = 0; mu < K1; ++mu) out[(long)K1 * a.Mv + (long)mu * a.Mp + node] += acc[mu];
     }
   }
 }

@@ -102,6 +102,11 @@ struct Level {
   int* d_face_off = nullptr;   // ncells+1: first boundary face of every (linear) cell
   int* d_face_cell = nullptr;  // nfaces: linear cell of each boundary face
   unsigned char* d_face_side = nullptr;  // nfaces: side (2*axis + upper) of each boundary face
+  // face gather lists: nodes of the boundary-cell layer (velocity first, then pressure)
+  int n_gather = 0, n_gather_vel = 0;
+  int* d_gnode = nullptr;
+  int* d_gptr = nullptr;
+  void* d_gent = nullptr;
   // Vanka / coarse operator storage (set up by the preconditioner)
 };
 

@@ -69,11 +69,12 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   e = cudaEventRecord(h->ev_join, h->s_face);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   if (e != cudaSuccess) return e;
-  if (MODE != OP_LIN && nslots > 0) {
-    const long nn = L.Nq2 + L.Nq1;
-    long g = (nn + 255) / 256;
+  if (MODE != OP_LIN && nslots > 0 && L.n_gather > 0) {
+    long g = (L.n_gather + 255) / 256;
     if (g > 16L * h->nsm) g = 16L * h->nsm;
-    st_face_gather<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(a, L.d_face_off, fscr, reinterpret_cast<T*>(a.out));
+    st_face_gather<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(
+        a, L.n_gather_vel, L.d_gnode, L.d_gptr, reinterpret_cast<const GatherEnt*>(L.d_gent), L.n_gather, fscr,
+        reinterpret_cast<T*>(a.out));
     e = cudaGetLastError();
   }
   return e;
