@@ -1,0 +1,163 @@
+"""Oracle for the space-time multigrid preconditioner (Sec. 6.3).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain numpy/scipy
+restatement on the oracle's assembled matrices, small meshes only:
+
+  prolongation       nested Q2/Q1 transfer P: coarse finite-element function
+                     evaluated at the fine nodes; identity in time (same k on
+                     all levels); restriction = P^T
+  galerkin           A_l = P^T A_{l+1} P (Petrov-Galerkin with Pi = P^T)
+  patch_dofs         cell patch K: every velocity and pressure dof of cell K at
+                     every Radau node (the full time-step block)
+  exact_patch        A_{l,K} = R_K A_l R_K^T
+  surrogate_operator finest level: the slab operator with every node's state
+                     replaced by u_rep = sum_mu l_mu(t_rep) V_mu, t_rep the slab
+                     midpoint (eq. surrogate-diag: diag(J_1..J_{k+1}) ->
+                     I (x) J^rep, temporal matrices unchanged)
+  vanka_step         d <- d + omega sum_K R_K^T A_K^{-1} R_K (r - A d)
+                     (eq. stmg-vanka-update), one defect per step
+  vcycle             pre-smoothing, restriction, recursion, coarsest-level
+                     treatment, prolongation, post-smoothing
+Readings (the paper defers to its references here): the coarsest level is
+treated by `coarse_sweeps` additive Vanka steps with exact patches starting
+from zero; patches are cell patches; omega is a scalar.
+"""
+import numpy as np
+import scipy.sparse as sp
+
+from . import (EXN, MODN, PIC, T_ALL, assemble_csr, cell_dofs, gauss01, sizes,  # noqa: F401
+               time_tables)
+
+
+def coarse_params(p, levels_down=1):
+    q = dict(p)
+    f = 2 ** levels_down
+    q["nx"] //= f
+    q["ny"] //= f
+    if p["dim"] == 3:
+        q["nz"] //= f
+    return q
+
+
+def _lagrange(nodes, i, x):
+    r = 1.0
+    for j, xj in enumerate(nodes):
+        if j != i:
+            r *= (x - xj) / (nodes[i] - xj)
+    return r
+
+
+def prolongation_1d(nc, order):
+    """1D global prolongation (fine nodes x coarse nodes) for Q2 (order 2) or
+    Q1 (order 1) on nc coarse cells: the coarse basis evaluated at the fine nodes."""
+    loc = [0.0, 0.5, 1.0] if order == 2 else [0.0, 1.0]
+    nf_nodes = order * 2 * nc + 1
+    nc_nodes = order * nc + 1
+    P = np.zeros((nf_nodes, nc_nodes))
+    for i in range(nf_nodes):
+        x = i / (order * 2.0)  # position in coarse-cell units
+        e = min(int(np.floor(x)), nc - 1)
+        xi = x - e
+        for a in range(order + 1):
+            P[i, order * e + a] = _lagrange(loc, a, xi)
+    return P
+
+
+def prolongation(pc):
+    """Slab prolongation from the mesh of pc to the twice finer mesh."""
+    d = pc["dim"]
+    K1 = pc["k"] + 1
+    n = [pc["nx"], pc["ny"]] + ([pc["nz"]] if d == 3 else [])
+    P2 = [prolongation_1d(m, 2) for m in n]
+    P1 = [prolongation_1d(m, 1) for m in n]
+    # lexicographic, x fastest: kron(Pz, Py, Px)
+    Pv = P2[-1]
+    for m in reversed(P2[:-1]):
+        Pv = np.kron(Pv, m)
+    Pp = P1[-1]
+    for m in reversed(P1[:-1]):
+        Pp = np.kron(Pp, m)
+    Pv = sp.csr_matrix(Pv)
+    Pp = sp.csr_matrix(Pp)
+    blocks = [Pv] * (K1 * d) + [Pp] * K1
+    return sp.block_diag(blocks, format="csr")
+
+
+def galerkin(A, P):
+    return (P.T @ A @ P).tocsr()
+
+
+def patch_dofs(p, cell):
+    return cell_dofs(p, [cell])[0]
+
+
+def exact_patch(A, dofs):
+    return A[dofs][:, dofs].toarray()
+
+
+def rep_state(p, U):
+    """Velocity at the slab midpoint t_rep in every node; pressure kept."""
+    s = sizes(p)
+    K1 = p["k"] + 1
+    T = time_tables(p["k"])
+    lrep = np.array([_lagrange(T["t"], i, 0.5) for i in range(K1)])
+    V = U[: K1 * s["Mv"]].reshape(K1, -1)
+    urep = lrep @ V
+    Ur = U.copy()
+    for mu in range(K1):
+        Ur[mu * s["Mv"]:(mu + 1) * s["Mv"]] = urep
+    return Ur
+
+
+def surrogate_operator(p, var, U):
+    """Global operator whose cell patches are the surrogate patches of eq. surrogate-diag."""
+    return assemble_csr(p, var, rep_state(p, U))
+
+
+class Hierarchy:
+    """Levels 0 (coarsest) .. L (finest) with operators and patch inverses."""
+
+    def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True):
+        self.levels = levels
+        self.omega = omega
+        self.pre, self.post, self.coarse_sweeps = pre, post, coarse_sweeps
+        self.params = [coarse_params(p, levels - 1 - l) for l in range(levels)]
+        self.A = [None] * levels
+        self.P = [None] * levels  # P[l]: level l-1 -> level l
+        self.A[-1] = assemble_csr(p, var, U)
+        for l in range(levels - 1, 0, -1):
+            self.P[l] = prolongation(self.params[l - 1])
+            self.A[l - 1] = galerkin(self.A[l], self.P[l])
+        self.Ainv = []
+        self.dofs = []
+        for l in range(levels):
+            pl = self.params[l]
+            ncell = sizes(pl)["ncells"]
+            D = cell_dofs(pl, np.arange(ncell))
+            src = surrogate_operator(p, var, U) if (l == levels - 1 and surrogate) else self.A[l]
+            self.dofs.append(D)
+            self.Ainv.append([np.linalg.inv(exact_patch(src, D[c])) for c in range(ncell)])
+
+    def vanka_step(self, l, r, d):
+        A = self.A[l]
+        defect = r - A @ d
+        corr = np.zeros_like(d)
+        for c, dof in enumerate(self.dofs[l]):
+            corr[dof] += self.Ainv[l][c] @ defect[dof]
+        return d + self.omega * corr
+
+    def smooth(self, l, r, d, sweeps):
+        for _ in range(sweeps):
+            d = self.vanka_step(l, r, d)
+        return d
+
+    def vcycle(self, r, l=None):
+        if l is None:
+            l = self.levels - 1
+        d = np.zeros_like(r)
+        if l == 0:
+            return self.smooth(0, r, d, self.coarse_sweeps)
+        d = self.smooth(l, r, d, self.pre)
+        rc = self.P[l].T @ (r - self.A[l] @ d)
+        d = d + self.P[l] @ self.vcycle(rc, l - 1)
+        return self.smooth(l, r, d, self.post)
