@@ -86,6 +86,7 @@ typedef struct {
   double lin_rtol;            /* fixed relative FGMRES tolerance (Picard)            */
   double ew_gamma, ew_alpha, ew_max; /* Eisenstat-Walker forcing, eq. nk-inexact-newton */
   double armijo_c, lambda_min;/* Armijo backtracking on phi = 1/2 |R|_M^2 (Sec. 6.2) */
+  int coarse_sweeps;          /* Vanka sweeps (exact patches) on the coarsest level  */
 } st_params;
 
 typedef struct {

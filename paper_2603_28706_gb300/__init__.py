@@ -36,7 +36,8 @@ class StParams(ctypes.Structure):
                 ("fgmres_restart", ctypes.c_int), ("fgmres_maxit", ctypes.c_int), ("newton_maxit", ctypes.c_int),
                 ("tol_abs", ctypes.c_double), ("tol_rel", ctypes.c_double), ("lin_rtol", ctypes.c_double),
                 ("ew_gamma", ctypes.c_double), ("ew_alpha", ctypes.c_double), ("ew_max", ctypes.c_double),
-                ("armijo_c", ctypes.c_double), ("lambda_min", ctypes.c_double)]
+                ("armijo_c", ctypes.c_double), ("lambda_min", ctypes.c_double),
+                ("coarse_sweeps", ctypes.c_int)]
 
 
 class StNewtonInfo(ctypes.Structure):

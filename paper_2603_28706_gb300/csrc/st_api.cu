@@ -268,6 +268,9 @@ void fill_op_args(const st_problem* h, int level, OpArgs& a) {
   a.inflow = P.inflow_profile;
   a.face_off = L.d_face_off;
   a.err = h->d_err;
+  for (int c = 0; c < 9; ++c) a.col_start_all[c] = L.col_start[c];
+  for (int c = 0; c < 8; ++c)
+    for (int d = 0; d < 3; ++d) a.cn_all[c][d] = L.cn[c][d];
 }
 
 cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent, const void* in, void* out,
@@ -374,6 +377,7 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 16 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, h->scratch_len * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_work, 3 * (size_t)F.Nst * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_Ulin, (size_t)F.Nst * sizeof(double));
   {
     const int nout = h->dim == 3 ? 2 * 3 * 9 + 4 : 2 * 2 * 3 + 2;
     const size_t nf = (size_t)(F.nfaces > 0 ? F.nfaces : 1) * h->K1 * nout;
@@ -409,6 +413,7 @@ st_status st_destroy(st_problem* h) {
   cudaFree(h->d_err);
   cudaFree(h->d_scratch);
   cudaFree(h->d_work);
+  cudaFree(h->d_Ulin);
   cudaFree(h->d_fscr);
   if (h->s_face) cudaStreamDestroy(h->s_face);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -443,7 +448,10 @@ st_status st_linearize(st_problem* h, st_tangent tangent, const void* U) {
   if (!U) return set_error(h, ST_EINVAL, "st_linearize: U is required");
   if (tangent < ST_PIC || tangent > ST_MODN) return set_error(h, ST_EINVAL, "st_linearize: bad tangent");
   const int L = (int)h->lev.size() - 1;
-  st_status s = cuda_check(h, launch_op(h, L, OP_LIN, ST_FP64, tangent, U, nullptr, nullptr, nullptr), "st_linearize");
+  st_status s = cuda_check(h, cudaMemcpyAsync(h->d_Ulin, U, h->lev[L].Nst * sizeof(double), cudaMemcpyDeviceToDevice,
+                                              h->stream), "st_linearize copy");
+  if (s != ST_OK) return s;
+  s = cuda_check(h, launch_op(h, L, OP_LIN, ST_FP64, tangent, U, nullptr, nullptr, nullptr), "st_linearize");
   if (s != ST_OK) return s;
   s = cuda_check(h, cast_f64_f32(h->d_cache64, h->d_cache32, h->cache_len, h->stream), "st_linearize cast");
   if (s != ST_OK) return s;

@@ -486,4 +486,113 @@ __global__ void st_face_gather(const OpArgs a, int nvel, const int* __restrict__
   }
 }
 
+
+// Boundary-face part of the spatial element matrices (added into E): one CTA
+// per boundary cell handles all faces of that cell in turn, so no two CTAs add
+// into the same matrix.  For every trial dof j the face-point values of the
+// trial function are set up, the same pointwise face terms as the Jacobian
+// action (face_point, OP_JAC) are evaluated, and the results are integrated
+// against every test function of the cell.
+template <int DIM, int K1, typename T, int TAN>
+__global__ void __launch_bounds__(OP_THREADS) st_face_matrix(const OpArgs a, const int* __restrict__ bcells, int nbc,
+                                                             T* __restrict__ E) {
+  using D = Dims<DIM>;
+  using Cfg = FaceCfg<DIM, T>;
+  constexpr int NC = D::NC, NQ = D::NQ, NFQ = D::NFQ, NE = D::NE, NFP = D::NFP, PS = Cfg::per_slot;
+  const auto& ct = CT<T>::t();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sW = reinterpret_cast<T*>(smem_raw);  // NE workspaces of PS entries
+  __shared__ double sDn[9];                // Q2 basis derivative at the Gauss points, [q][a]
+  if (threadIdx.x < 9) {
+    const int q = threadIdx.x / 3, aa = threadIdx.x % 3;
+    double v = 0.0;
+    for (int r = 0; r < 3; ++r) v += cT.Dc[q * 3 + r] * cT.B[r * 3 + aa];
+    sDn[threadIdx.x] = v;
+  }
+  __syncthreads();
+  const int mu = a.elm_mu;
+  for (int b = blockIdx.x; b < nbc; b += gridDim.x) {
+    const int cell = bcells[b];
+    const int e3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1], (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0};
+    int rank = 0;
+    for (int side = 0; side < 2 * DIM; ++side) {
+      const int ax = side >> 1, up = side & 1;
+      const bool on = up ? (e3[ax] == a.n[ax] - 1) : (e3[ax] == 0);
+      if (!on) continue;
+      const int fid = a.face_off[cell] + rank++;
+      const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+      // (1) trial values at the face points
+      for (int it = threadIdx.x; it < NE * NFQ; it += blockDim.x) {
+        const int j = it / NFQ, fq = it % NFQ;
+        T* w = sW + j * PS;
+        const int i1 = fq % 3, i2 = (DIM == 3) ? fq / 3 : 0;
+        for (int c = 0; c < NC; ++c) {
+          w[Cfg::oPV + c * NFQ + fq] = 0;
+          w[Cfg::oPN + c * NFQ + fq] = 0;
+          for (int td = 0; td < DIM - 1; ++td) w[Cfg::oPT + (c * (DIM - 1) + td) * NFQ + fq] = 0;
+        }
+        if (fq == 0)
+          for (int m = 0; m < NFP; ++m) w[Cfg::oFP + m] = 0;
+        if (j < NC * NQ) {
+          const int c = j / NQ, n = j % NQ;
+          const int nn[3] = {n % 3, (n / 3) % 3, (DIM == 3) ? n / 9 : 0};
+          const double en = cT.E[up * 3 + nn[ax]], edn = cT.ED[up * 3 + nn[ax]] * a.ih[ax];
+          const double b1 = cT.B[i1 * 3 + nn[t1]], d1 = sDn[i1 * 3 + nn[t1]] * a.ih[t1];
+          const double b2 = (DIM == 3) ? cT.B[i2 * 3 + nn[t2]] : 1.0;
+          const double d2 = (DIM == 3) ? sDn[i2 * 3 + nn[t2]] * a.ih[t2] : 0.0;
+          w[Cfg::oPV + c * NFQ + fq] = (T)(en * b1 * b2);
+          w[Cfg::oPN + c * NFQ + fq] = (T)(edn * b1 * b2);
+          w[Cfg::oPT + (c * (DIM - 1) + 0) * NFQ + fq] = (T)(en * d1 * b2);
+          if (DIM == 3) w[Cfg::oPT + (c * (DIM - 1) + 1) * NFQ + fq] = (T)(en * b1 * d2);
+        } else if (fq == 0) {
+          const int m = j - NC * NQ;  // trial pressure node; on the face?
+          const int mm[3] = {m & 1, (m >> 1) & 1, (DIM == 3) ? (m >> 2) : 0};
+          if (mm[ax] == up) w[Cfg::oFP + (mm[t1] + 2 * ((DIM == 3) ? mm[t2] : 0))] = 1;
+        }
+      }
+      __syncthreads();
+      // (2) pointwise face terms, fluxes in place
+      for (int it = threadIdx.x; it < NE * NFQ; it += blockDim.x) {
+        const int j = it / NFQ, fq = it % NFQ;
+        T* w = sW + j * PS;
+        if (ax == 0) face_point<DIM, K1, T, OP_JAC, TAN, 0>(a, w, fq, side, mu, cell, fid);
+        else if (ax == 1) face_point<DIM, K1, T, OP_JAC, TAN, 1>(a, w, fq, side, mu, cell, fid);
+        else if constexpr (DIM == 3) face_point<DIM, K1, T, OP_JAC, TAN, 2>(a, w, fq, side, mu, cell, fid);
+      }
+      __syncthreads();
+      // (3) integrate against every test function: E[i][j] += ...
+      T* Ec = E + ((long)cell * a.elm_stride + a.elm_slot) * NE * NE;
+      for (int it = threadIdx.x; it < NE * NE; it += blockDim.x) {
+        const int i = it / NE, j = it % NE;
+        const T* w = sW + j * PS;
+        T acc = 0;
+        if (i < NC * NQ) {
+          const int c = i / NQ, n = i % NQ;
+          const int nn[3] = {n % 3, (n / 3) % 3, (DIM == 3) ? n / 9 : 0};
+          const double en = cT.E[up * 3 + nn[ax]], edn = cT.ED[up * 3 + nn[ax]] * a.ih[ax];
+          if (en == 0.0 && edn == 0.0) continue;
+          for (int fq = 0; fq < NFQ; ++fq) {
+            const int i1 = fq % 3, i2 = (DIM == 3) ? fq / 3 : 0;
+            const double b1 = cT.B[i1 * 3 + nn[t1]], d1 = sDn[i1 * 3 + nn[t1]] * a.ih[t1];
+            const double b2 = (DIM == 3) ? cT.B[i2 * 3 + nn[t2]] : 1.0;
+            const double d2 = (DIM == 3) ? sDn[i2 * 3 + nn[t2]] * a.ih[t2] : 0.0;
+            acc += w[Cfg::oPV + c * NFQ + fq] * (T)(en * b1 * b2) + w[Cfg::oPN + c * NFQ + fq] * (T)(edn * b1 * b2) +
+                   w[Cfg::oPT + (c * (DIM - 1) + 0) * NFQ + fq] * (T)(en * d1 * b2);
+            if (DIM == 3) acc += w[Cfg::oPT + (c * (DIM - 1) + 1) * NFQ + fq] * (T)(en * b1 * d2);
+          }
+        } else {
+          const int m = i - NC * NQ;
+          const int mm[3] = {m & 1, (m >> 1) & 1, (DIM == 3) ? (m >> 2) : 0};
+          if (mm[ax] != up) continue;
+          const int mf = mm[t1] + 2 * ((DIM == 3) ? mm[t2] : 0);
+          for (int fq = 0; fq < NFQ; ++fq)
+            acc += ((DIM == 3) ? ct.FPSI3[fq * 4 + mf] : ct.FPSI2[fq * 2 + mf]) * w[Cfg::oFQ + fq];
+        }
+        Ec[(long)i * NE + j] += acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace st

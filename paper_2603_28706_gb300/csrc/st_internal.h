@@ -73,9 +73,15 @@ struct OpArgs {
   double* wfcache;
   const int* face_off;     // first boundary face of every cell (linear order)
   int* err;                // device error flag
+  // element-matrix mode: all colour classes, fixed node mu, output matrices
+  long col_start_all[9];
+  int cn_all[8][3];
+  int elm_mu;              // coefficient-cache node of the matrices
+  int elm_stride;          // matrices per cell in the output
+  int elm_slot;            // which of them is written
 };
 
-enum OpMode { OP_LIN = 0, OP_JAC = 1, OP_RES = 2 };
+enum OpMode { OP_LIN = 0, OP_JAC = 1, OP_RES = 2, OP_ELM = 3 };
 
 template <int DIM> struct Dims {
   static constexpr int NQ = DIM == 3 ? 27 : 9;
@@ -131,6 +137,7 @@ struct st_problem {
   double* d_scratch = nullptr;     // small reduction scratch
   size_t scratch_len = 0;
   double* d_work = nullptr;        // 3 finest-level slab vectors (mass operator work)
+  double* d_Ulin = nullptr;        // copy of the state of the last linearisation
   double* d_fscr = nullptr;         // compact per-face-slot outputs of the face kernel (FP64 or FP32 view)
   cudaStream_t s_face = nullptr;   // internal stream: face kernels overlap the volume kernels
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -1,32 +1,951 @@
-// Multigrid preconditioner: surrogate Vanka patches, Galerkin coarse
-// operators, transfers, V-cycle (Sec. 6.3).
+// Space-time multigrid preconditioner (Sec. 6.3): nested Q2/Q1 transfers,
+// Galerkin coarse operators, exact and surrogate cell patches, batched LU,
+// additive Vanka sweeps and the V-cycle.
+//
+// Data per level l (0 = coarsest, L = finest):
+//   E_l   spatial element matrices (times tau w_mu) of every cell and node mu,
+//         [ncells][K1][NE][NE]: on level L from the coefficient cache of the
+//         current linearisation (volume by unit-vector probing of the
+//         sum-factorised operator, faces directly), on l < L by Galerkin
+//         coarsening E_l = sum_children P_c^T E_{l+1} P_c (exact for nested
+//         spaces, identity in time, so A_l = P^T A_{l+1} P);
+//   LU_l  LU factors (partial pivoting, column-major) of the cell patches
+//         A_{l,K} = R_K A_l R_K^T (l < L) resp. the surrogate A~_{L,K}
+//         (eq. surrogate-diag: every node's spatial block replaced by the one
+//         at t_rep = slab midpoint, temporal matrices unchanged).
+// Patch size N = (k+1) NE (all velocity and pressure dofs of the cell at all
+// Radau nodes).  A Vanka step computes the defect r - A_l d once, solves all
+// patches and adds omega times their corrections into d, colour class by
+// colour class (cells of one class share no dof), eq. stmg-vanka-update.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "st_blas.cuh"
 #include "st_internal.h"
 
 namespace st {
+
+cudaError_t dispatch_elm_2d(const st_problem* h, const Level& L, const OpArgs& a, int prec, int tangent, void* E,
+                            const int* bcells, int nbc);
+cudaError_t dispatch_elm_3d(const st_problem* h, const Level& L, const OpArgs& a, int prec, int tangent, void* E,
+                            const int* bcells, int nbc);
+
+namespace {
+
+constexpr int MAXN = 4 * 89;  // largest patch size (k = 3, 3D)
+
+int ne_of(int dim) { return dim == 3 ? 3 * 27 + 8 : 2 * 9 + 4; }
+
+// ------------------------------------------------------------- transfers
+// One direction of the nested prolongation on blocks of a tensor grid:
+// input grid gi (coarse along dir), output grid go (fine along dir).  ORDER 2
+// (Q2: 2nc+1 -> 4nc+1 points) or 1 (Q1: nc+1 -> 2nc+1).  Fine point i lies in
+// coarse cell e = min(i / (2 ORDER), nc - 1) at local position r = i - 2 ORDER e.
+template <typename T, int ORDER>
+__global__ void prolong_pass(const T* __restrict__ x, T* __restrict__ y, int gi0, int gi1, int gi2, int dir, int nc,
+                             int nblk, const double* __restrict__ P) {
+  const int go[3] = {dir == 0 ? 2 * ORDER * nc + 1 : gi0, dir == 1 ? 2 * ORDER * nc + 1 : gi1,
+                     dir == 2 ? 2 * ORDER * nc + 1 : gi2};
+  const long nout = (long)go[0] * go[1] * go[2];
+  const long nin = (long)gi0 * gi1 * gi2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nout * nblk; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / nout, r = t % nout;
+    int idx[3] = {(int)(r % go[0]), (int)((r / go[0]) % go[1]), (int)(r / ((long)go[0] * go[1]))};
+    const int i = idx[dir];
+    int e = i / (2 * ORDER);
+    if (e > nc - 1) e = nc - 1;
+    const int loc = i - 2 * ORDER * e;
+    T acc = 0;
+    for (int aa = 0; aa <= ORDER; ++aa) {
+      idx[dir] = ORDER * e + aa;
+      const long src = idx[0] + (long)gi0 * (idx[1] + (long)gi1 * idx[2]);
+      acc += (T)P[loc * (ORDER + 1) + aa] * x[b * nin + src];
+    }
+    y[t] = acc;
+  }
+}
+
+// One direction of the restriction P^T (gather form): coarse point j collects
+// every fine point whose coarse cell contains it.
+template <typename T, int ORDER>
+__global__ void restrict_pass(const T* __restrict__ x, T* __restrict__ y, int gi0, int gi1, int gi2, int dir, int nc,
+                              int nblk, const double* __restrict__ P) {
+  const int go[3] = {dir == 0 ? ORDER * nc + 1 : gi0, dir == 1 ? ORDER * nc + 1 : gi1, dir == 2 ? ORDER * nc + 1 : gi2};
+  const long nout = (long)go[0] * go[1] * go[2];
+  const long nin = (long)gi0 * gi1 * gi2;
+  const int gid = dir == 0 ? gi0 : (dir == 1 ? gi1 : gi2);
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nout * nblk; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / nout, r = t % nout;
+    int idx[3] = {(int)(r % go[0]), (int)((r / go[0]) % go[1]), (int)(r / ((long)go[0] * go[1]))};
+    const int j = idx[dir];
+    T acc = 0;
+    for (int i = 2 * j - 2 * ORDER; i <= 2 * j + 2 * ORDER; ++i) {
+      if (i < 0 || i >= gid) continue;
+      int e = i / (2 * ORDER);
+      if (e > nc - 1) e = nc - 1;
+      const int aa = j - ORDER * e;
+      if (aa < 0 || aa > ORDER) continue;
+      const int loc = i - 2 * ORDER * e;
+      idx[dir] = i;
+      const long src = idx[0] + (long)gi0 * (idx[1] + (long)gi1 * idx[2]);
+      acc += (T)P[loc * (ORDER + 1) + aa] * x[b * nin + src];
+    }
+    y[t] = acc;
+  }
+}
+
+// ------------------------------------------------------------- Galerkin
+// E_c[cell][mu] = sum over the 2^d children of P_ch^T E_f[child][mu] P_ch, with
+// P_ch the child-local-dof <- parent-local-dof prolongation (block diagonal:
+// one tensor Q2 block per velocity component, one Q1 block for the pressure).
+struct TransferTabs {
+  double P2[15], P1[6];
+};
+
+double pch(int DIM, const TransferTabs& tt, int j, int b, const int off[3]) {
+  // j: child-local dof, b: parent-local dof
+  const int NQ = DIM == 3 ? 27 : 9, NC = DIM;
+  const bool vj = j < NC * NQ, vb = b < NC * NQ;
+  if (vj != vb) return 0.0;
+  if (vj) {
+    if (j / NQ != b / NQ) return 0.0;
+    const int n = j % NQ, m = b % NQ;
+    const int ni[3] = {n % 3, (n / 3) % 3, n / 9}, mi[3] = {m % 3, (m / 3) % 3, m / 9};
+    double v = 1.0;
+    for (int d = 0; d < DIM; ++d) v *= tt.P2[(2 * off[d] + ni[d]) * 3 + mi[d]];
+    return v;
+  }
+  const int n = j - NC * NQ, m = b - NC * NQ;
+  const int ni[3] = {n & 1, (n >> 1) & 1, n >> 2}, mi[3] = {m & 1, (m >> 1) & 1, m >> 2};
+  double v = 1.0;
+  for (int d = 0; d < DIM; ++d) v *= tt.P1[(off[d] + ni[d]) * 2 + mi[d]];
+  return v;
+}
+
+template <int DIM, typename T>
+__global__ void galerkin_kernel(const T* __restrict__ Ef, T* __restrict__ Ec, int ncx, int ncy, int ncz, int K1,
+                                const double* __restrict__ Pch) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NE = NC * NQ + (DIM == 3 ? 8 : 4);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sE = reinterpret_cast<T*>(smraw);  // child matrix
+  T* sT = sE + NE * NE;                  // E_f P
+  T* sR = sT + NE * NE;                  // result
+  const long ncell = (long)ncx * ncy * ncz;
+  const int nfx = 2 * ncx, nfy = 2 * ncy;
+  for (long item = blockIdx.x; item < ncell * K1; item += gridDim.x) {
+    const long cc = item / K1;
+    const int mu = (int)(item % K1);
+    const int cx = (int)(cc % ncx), cy = (int)((cc / ncx) % ncy), cz = (int)(cc / ((long)ncx * ncy));
+    for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) sR[i] = 0;
+    for (int ch = 0; ch < (1 << DIM); ++ch) {
+      const int off[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+      const long fcell = (2 * cx + off[0]) + (long)nfx * ((2 * cy + off[1]) + (long)nfy * (DIM == 3 ? 2 * cz + off[2] : 0));
+      const T* src = Ef + (fcell * K1 + mu) * NE * NE;
+      const double* sP = Pch + (long)ch * NE * NE;
+      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) sE[i] = src[i];
+      __syncthreads();
+      // T = E_f P (P block diagonal: only same-block columns contribute)
+      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) {
+        const int r = i / NE, b = i % NE;
+        const int j0 = b < NC * NQ ? (b / NQ) * NQ : NC * NQ, j1 = b < NC * NQ ? j0 + NQ : NE;
+        T acc = 0;
+        for (int j = j0; j < j1; ++j) acc += sE[r * NE + j] * (T)sP[j * NE + b];
+        sT[i] = acc;
+      }
+      __syncthreads();
+      // R += P^T T
+      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) {
+        const int aa = i / NE, b = i % NE;
+        const int j0 = aa < NC * NQ ? (aa / NQ) * NQ : NC * NQ, j1 = aa < NC * NQ ? j0 + NQ : NE;
+        T acc = 0;
+        for (int j = j0; j < j1; ++j) acc += (T)sP[j * NE + aa] * sT[j * NE + b];
+        sR[i] += acc;
+      }
+      __syncthreads();
+    }
+    T* dst = Ec + (cc * K1 + mu) * NE * NE;
+    for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) dst[i] = sR[i];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- patch assembly
+// A_K (N x N, column-major F[col][row]) for cell K:
+//   block (mu, nu): K_t[mu][nu] M_K (velocity part) + delta_{mu nu} S_mu,
+//   S_mu = sum over the neighbour cells e of K of E[e][mu] restricted to the
+//   dofs of K (surrogate: S_mu = (w_mu / w_0) sum_e Erep[e]).
+// Velocity dof (c, node a in {0,1,2}^d of K) is node a - 2 delta in a
+// neighbour shifted by delta in {-1,0,1}^d; pressure node m is m - delta.
+struct PatchArgs {
+  int n[3];
+  int K1;
+  double Kt[16];
+  double wr[4];        // w_mu / w_0 (surrogate) or 1
+  double M1h[3][9];    // 1D Q2 mass matrices scaled by h
+  int surrogate;
+};
+
+template <int DIM>
+__device__ __forceinline__ bool local_in(int dof, const int dl[3], int& out) {
+  // dof of K -> local dof in the neighbour shifted by dl (false if not shared)
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM;
+  if (dof < NC * NQ) {
+    const int c = dof / NQ, n = dof % NQ;
+    int ni[3] = {n % 3, (n / 3) % 3, n / 9};
+    for (int d = 0; d < DIM; ++d) {
+      ni[d] -= 2 * dl[d];
+      if (ni[d] < 0 || ni[d] > 2) return false;
+    }
+    out = c * NQ + ni[0] + 3 * ni[1] + 9 * ni[2];
+    return true;
+  }
+  const int m = dof - NC * NQ;
+  int mi[3] = {m & 1, (m >> 1) & 1, m >> 2};
+  for (int d = 0; d < DIM; ++d) {
+    mi[d] -= dl[d];
+    if (mi[d] < 0 || mi[d] > 1) return false;
+  }
+  out = NC * NQ + mi[0] + 2 * mi[1] + 4 * mi[2];
+  return true;
+}
+
+template <int DIM, typename T>
+__global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs pa, T* __restrict__ F) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NE = NC * NQ + (DIM == 3 ? 8 : 4);
+  const int K1 = pa.K1, N = K1 * NE;
+  const long ncell = (long)pa.n[0] * pa.n[1] * (DIM == 3 ? pa.n[2] : 1);
+  for (long K = blockIdx.x; K < ncell; K += gridDim.x) {
+    const int k3[3] = {(int)(K % pa.n[0]), (int)((K / pa.n[0]) % pa.n[1]),
+                       DIM == 3 ? (int)(K / ((long)pa.n[0] * pa.n[1])) : 0};
+    T* Fk = F + K * (long)N * N;
+    for (int it = threadIdx.x; it < NE * NE; it += blockDim.x) {
+      const int p = it / NE, q = it % NE;  // row, column within a spatial block
+      // spatial block sums (per mu) and the velocity mass entry
+      T S[4] = {0, 0, 0, 0};
+      double mass = 0.0;
+      const bool vel_pair = p < NC * NQ && q < NC * NQ && (p / NQ) == (q / NQ);
+      for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int dl[3] = {dx, dy, dz};
+            const int e3[3] = {k3[0] + dx, k3[1] + dy, k3[2] + dz};
+            bool inside = true;
+            for (int d = 0; d < DIM; ++d) inside = inside && e3[d] >= 0 && e3[d] < pa.n[d];
+            if (!inside) continue;
+            int lp, lq;
+            if (!local_in<DIM>(p, dl, lp) || !local_in<DIM>(q, dl, lq)) continue;
+            const long ecell = e3[0] + (long)pa.n[0] * (e3[1] + (long)pa.n[1] * e3[2]);
+            if (pa.surrogate) {
+              const T v = E[(ecell * estride) * NE * NE + (long)lp * NE + lq];
+              for (int mu = 0; mu < K1; ++mu) S[mu] += (T)pa.wr[mu] * v;
+            } else {
+              for (int mu = 0; mu < K1; ++mu) S[mu] += E[(ecell * estride + mu) * NE * NE + (long)lp * NE + lq];
+            }
+            if (vel_pair) {
+              const int a = lp % NQ, b = lq % NQ;
+              const int ai[3] = {a % 3, (a / 3) % 3, a / 9}, bi[3] = {b % 3, (b / 3) % 3, b / 9};
+              double m = 1.0;
+              for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
+              mass += m;
+            }
+          }
+      for (int mu = 0; mu < K1; ++mu)
+        for (int nu = 0; nu < K1; ++nu) {
+          T v = (mu == nu) ? S[mu] : (T)0;
+          if (vel_pair) v += (T)(pa.Kt[mu * K1 + nu] * mass);
+          // column-major: F[col][row]
+          Fk[(long)(nu * NE + q) * N + (mu * NE + p)] = v;
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ batched LU
+// In-place LU with partial pivoting of `count` matrices of size N stored
+// column-major (F[col][row]); one CTA per matrix.  A zero pivot sets err[0].
+template <typename T>
+__global__ void lu_kernel(T* __restrict__ F, int* __restrict__ piv, int N, long count, int* __restrict__ err) {
+  __shared__ int s_piv;
+  __shared__ T s_val[256];
+  __shared__ int s_idx[256];
+  for (long m = blockIdx.x; m < count; m += gridDim.x) {
+    T* A = F + m * (long)N * N;
+    for (int k = 0; k < N; ++k) {
+      // pivot search in column k, rows k..N-1
+      T best = -1;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < N; i += blockDim.x) {
+        const T v = fabs(A[(long)k * N + i]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+      s_val[threadIdx.x] = best;
+      s_idx[threadIdx.x] = bi;
+      __syncthreads();
+      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+          const T o = s_val[threadIdx.x + w];
+          const int oi = s_idx[threadIdx.x + w];
+          if (o > s_val[threadIdx.x] || (o == s_val[threadIdx.x] && oi < s_idx[threadIdx.x])) {
+            s_val[threadIdx.x] = o;
+            s_idx[threadIdx.x] = oi;
+          }
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        s_piv = s_idx[0];
+        piv[m * N + k] = s_piv;
+        if (!(s_val[0] > 0)) atomicExch(err, 1);
+      }
+      __syncthreads();
+      const int p = s_piv;
+      if (p != k)
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+          const T t = A[(long)j * N + k];
+          A[(long)j * N + k] = A[(long)j * N + p];
+          A[(long)j * N + p] = t;
+        }
+      __syncthreads();
+      const T d = A[(long)k * N + k];
+      const T inv = d != (T)0 ? (T)1 / d : (T)0;
+      for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) A[(long)k * N + i] *= inv;
+      __syncthreads();
+      const int rem = N - k - 1;
+      for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
+        const int jj = k + 1 + t / rem, ii = k + 1 + t % rem;
+        A[(long)jj * N + ii] -= A[(long)k * N + ii] * A[(long)jj * N + k];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------ Vanka solve
+// For the patches (cells) of one colour class: x = A_K^{-1} defect|_K by the LU
+// factors, then d|_K += omega x (cells of one class share no dof).
+template <int DIM, typename T>
+__global__ void vanka_patch_solve(const T* __restrict__ F, const int* __restrict__ piv, int K1, const T* __restrict__ defect,
+                                  T* __restrict__ d, int n0, int n1, int n2, int c0x, int c0y, int c0z, int cnx, int cny,
+                                  long ncol, double omega, long Nq2, long Nq1, long Mv, long Mp) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
+  const int N = K1 * NE;
+  __shared__ T sx[MAXN];
+  __shared__ long sg[MAXN];
+  const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
+  for (long li = blockIdx.x; li < ncol; li += gridDim.x) {
+    const int ex = c0x + 2 * (int)(li % cnx), ey = c0y + 2 * (int)((li / cnx) % cny),
+              ez = DIM == 3 ? c0z + 2 * (int)(li / ((long)cnx * cny)) : 0;
+    const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
+    const T* A = F + cell * (long)N * N;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int mu = r / NE, loc = r % NE;
+      long g;
+      if (loc < NC * NQ) {
+        const int c = loc / NQ, q = loc % NQ;
+        g = (long)mu * Mv + c * Nq2 + (2L * ex + q % 3) + g2x * ((2L * ey + (q / 3) % 3) + g2y * (2L * ez + q / 9));
+      } else {
+        const int m = loc - NC * NQ;
+        g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+      }
+      sg[r] = g;
+      sx[r] = defect[g];
+    }
+    __syncthreads();
+    // row interchanges, in factorisation order
+    if (threadIdx.x == 0)
+      for (int k = 0; k < N; ++k) {
+        const int p = piv[cell * N + k];
+        if (p != k) {
+          const T t = sx[k];
+          sx[k] = sx[p];
+          sx[p] = t;
+        }
+      }
+    __syncthreads();
+    // forward substitution (unit lower), column oriented
+    for (int k = 0; k < N - 1; ++k) {
+      const T xk = sx[k];
+      for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) sx[i] -= A[(long)k * N + i] * xk;
+      __syncthreads();
+    }
+    // backward substitution
+    for (int k = N - 1; k >= 0; --k) {
+      if (threadIdx.x == 0) sx[k] /= A[(long)k * N + k];
+      __syncthreads();
+      const T xk = sx[k];
+      for (int i = threadIdx.x; i < k; i += blockDim.x) sx[i] -= A[(long)k * N + i] * xk;
+      __syncthreads();
+    }
+    for (int r = threadIdx.x; r < N; r += blockDim.x) d[sg[r]] += (T)omega * sx[r];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------- coarse-level apply
+// y += A_l x for the cells of one colour class: per cell and node mu the
+// element matrix E[cell][mu] (spatial part, times tau w_mu) and the temporal
+// mass coupling sum_nu K_t[mu][nu] M_e x_nu on the velocity.
+template <int DIM, typename T>
+__global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, const T* __restrict__ x, T* __restrict__ y,
+                             int c0x, int c0y, int c0z, int cnx, int cny, long ncol, long Nq2, long Nq1, long Mv,
+                             long Mp) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
+  __shared__ T sx[MAXN];
+  __shared__ long sg[MAXN];
+  const int N = K1 * NE;
+  const int n0 = pa.n[0], n1 = pa.n[1];
+  const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
+  for (long li = blockIdx.x; li < ncol; li += gridDim.x) {
+    const int ex = c0x + 2 * (int)(li % cnx), ey = c0y + 2 * (int)((li / cnx) % cny),
+              ez = DIM == 3 ? c0z + 2 * (int)(li / ((long)cnx * cny)) : 0;
+    const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int mu = r / NE, loc = r % NE;
+      long g;
+      if (loc < NC * NQ) {
+        const int c = loc / NQ, q = loc % NQ;
+        g = (long)mu * Mv + c * Nq2 + (2L * ex + q % 3) + g2x * ((2L * ey + (q / 3) % 3) + g2y * (2L * ez + q / 9));
+      } else {
+        const int m = loc - NC * NQ;
+        g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+      }
+      sg[r] = g;
+      sx[r] = x[g];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int mu = r / NE, i = r % NE;
+      const T* Er = E + (cell * K1 + mu) * NE * NE + (long)i * NE;
+      T acc = 0;
+      for (int j = 0; j < NE; ++j) acc += Er[j] * sx[mu * NE + j];
+      if (i < NC * NQ) {
+        const int c = i / NQ, a = i % NQ;
+        const int ai[3] = {a % 3, (a / 3) % 3, a / 9};
+        for (int b = 0; b < NQ; ++b) {
+          const int bi[3] = {b % 3, (b / 3) % 3, b / 9};
+          double m = 1.0;
+          for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
+          T s = 0;
+          for (int nu = 0; nu < K1; ++nu) s += (T)pa.Kt[mu * K1 + nu] * sx[nu * NE + c * NQ + b];
+          acc += (T)m * s;
+        }
+      }
+      y[sg[r]] += acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename A, typename B>
+__global__ void axpy_conv(const A* __restrict__ x, B* __restrict__ y, size_t n, double a, double b) {
+  // y = a * x + b * y  (b == 0: y = a * x)
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = b == 0.0 ? (B)(a * (double)x[i]) : (B)(a * (double)x[i] + b * (double)y[i]);
+}
+
+template <typename T>
+__global__ void sub_kernel(const T* __restrict__ r, const T* __restrict__ Ad, T* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = r[i] - Ad[i];
+}
+
+// U_rep: every node's velocity replaced by sum_mu lrep_mu V_mu; pressure copied
+__global__ void rep_state_kernel(const double* __restrict__ U, double* __restrict__ Ur, int K1, long Mv, long Np,
+                                 double l0, double l1, double l2, double l3) {
+  const double l[4] = {l0, l1, l2, l3};
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < Mv + Np; i += (long)gridDim.x * blockDim.x) {
+    if (i < Mv) {
+      double v = 0.0;
+      for (int mu = 0; mu < K1; ++mu) v += l[mu] * U[(long)mu * Mv + i];
+      for (int mu = 0; mu < K1; ++mu) Ur[(long)mu * Mv + i] = v;
+    } else {
+      const long j = i - Mv;
+      Ur[(long)K1 * Mv + j] = U[(long)K1 * Mv + j];
+    }
+  }
+}
+
+unsigned gridn(size_t n, int nsm) {
+  size_t g = (n + 255) / 256;
+  const size_t cap = 16 * (size_t)nsm;
+  if (g > cap) g = cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ state
+struct MgLevelData {
+  void* E = nullptr;    // [ncells][K1][NE][NE]
+  void* LU = nullptr;   // [ncells][N][N]
+  int* piv = nullptr;   // [ncells][N]
+  void* r = nullptr;    // level vectors (precision of the hierarchy)
+  void* d = nullptr;
+  void* t = nullptr;
+  void* t2 = nullptr;
+  void* t3 = nullptr;
+};
+
+struct MgState {
+  int prec = -1;
+  bool allocated = false;
+  std::vector<MgLevelData> L;
+  void* Erep = nullptr;          // finest surrogate matrices [ncells][NE][NE]
+  double* Urep = nullptr;        // representative state (slab vector)
+  double* cache_rep64 = nullptr;
+  double* fcache_rep64 = nullptr;
+  float* cache_rep32 = nullptr;
+  float* fcache_rep32 = nullptr;
+  int* bcells = nullptr;         // boundary cells (linear) of the finest level
+  int nbc = 0;
+  double* d_tab = nullptr;       // 1D transfer tables on the device (P2, P1)
+  double* d_pch = nullptr;       // child <- parent local prolongation matrices [2^d][NE][NE]
+};
+
+namespace {
+
+size_t esz(int prec) { return prec == ST_FP64 ? sizeof(double) : sizeof(float); }
+
+void free_mg(MgState* m) {
+  for (auto& l : m->L) {
+    cudaFree(l.E);
+    cudaFree(l.LU);
+    cudaFree(l.piv);
+    cudaFree(l.r);
+    cudaFree(l.d);
+    cudaFree(l.t);
+    cudaFree(l.t2);
+    cudaFree(l.t3);
+  }
+  m->L.clear();
+  cudaFree(m->Erep);
+  cudaFree(m->Urep);
+  cudaFree(m->cache_rep64);
+  cudaFree(m->fcache_rep64);
+  cudaFree(m->cache_rep32);
+  cudaFree(m->fcache_rep32);
+  cudaFree(m->bcells);
+  cudaFree(m->d_tab);
+  cudaFree(m->d_pch);
+  m->d_pch = nullptr;
+  m->Erep = nullptr;
+  m->Urep = nullptr;
+  m->cache_rep64 = m->fcache_rep64 = nullptr;
+  m->cache_rep32 = m->fcache_rep32 = nullptr;
+  m->bcells = nullptr;
+  m->d_tab = nullptr;
+  m->allocated = false;
+}
+
+cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
+  const int nl = (int)h->lev.size();
+  const int NE = ne_of(h->dim), K1 = h->K1, N = K1 * NE;
+  const size_t es = esz(prec);
+  m->L.resize(nl);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < nl && e == cudaSuccess; ++l) {
+    const Level& Lv = h->lev[l];
+    MgLevelData& d = m->L[l];
+    e = cudaMalloc(&d.E, (size_t)Lv.ncells * K1 * NE * NE * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.LU, (size_t)Lv.ncells * N * N * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.piv, (size_t)Lv.ncells * N * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d.r, (size_t)Lv.Nst * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.d, (size_t)Lv.Nst * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.t, (size_t)Lv.Nst * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.t2, (size_t)Lv.Nst * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.t3, (size_t)Lv.Nst * es);
+  }
+  const Level& F = h->lev.back();
+  if (e == cudaSuccess) e = cudaMalloc(&m->Erep, (size_t)F.ncells * NE * NE * es);
+  if (e == cudaSuccess) e = cudaMalloc(&m->Urep, (size_t)F.Nst * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->cache_rep64, h->cache_len * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->fcache_rep64, h->fcache_len * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->cache_rep32, h->cache_len * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->fcache_rep32, h->fcache_len * sizeof(float));
+  if (e == cudaSuccess) {
+    std::vector<int> bc;
+    for (long c = 0; c < F.ncells; ++c) {
+      const int e3[3] = {(int)(c % F.n[0]), (int)((c / F.n[0]) % F.n[1]), (int)(c / ((long)F.n[0] * F.n[1]))};
+      bool on = false;
+      for (int ax = 0; ax < h->dim; ++ax) on = on || e3[ax] == 0 || e3[ax] == F.n[ax] - 1;
+      if (on) bc.push_back((int)c);
+    }
+    m->nbc = (int)bc.size();
+    if (bc.empty()) bc.push_back(0);
+    e = cudaMalloc(&m->bcells, bc.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(m->bcells, bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    double tab[21];
+    memcpy(tab, h->R.P2, sizeof(h->R.P2));
+    memcpy(tab + 15, h->R.P1, sizeof(h->R.P1));
+    e = cudaMalloc(&m->d_tab, sizeof(tab));
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    TransferTabs tt;
+    memcpy(tt.P2, h->R.P2, sizeof(tt.P2));
+    memcpy(tt.P1, h->R.P1, sizeof(tt.P1));
+    const int nch = 1 << h->dim;
+    std::vector<double> P((size_t)nch * NE * NE);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int off[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+      for (int j = 0; j < NE; ++j)
+        for (int b = 0; b < NE; ++b) P[((size_t)ch * NE + j) * NE + b] = pch(h->dim, tt, j, b, off);
+    }
+    e = cudaMalloc(&m->d_pch, P.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_pch, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  m->prec = prec;
+  m->allocated = e == cudaSuccess;
+  return e;
+}
+
+PatchArgs patch_args(const st_problem* h, int level, bool surrogate) {
+  PatchArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  const Level& L = h->lev[level];
+  for (int d = 0; d < 3; ++d) pa.n[d] = L.n[d];
+  pa.K1 = h->K1;
+  for (int i = 0; i < h->K1 * h->K1; ++i) pa.Kt[i] = h->T.Kt[i];
+  for (int mu = 0; mu < h->K1; ++mu) pa.wr[mu] = surrogate ? h->T.w[mu] / h->T.w[0] : 1.0;
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < 9; ++i) pa.M1h[d][i] = h->R.M1[i] * (d < h->dim ? L.h[d] : 1.0);
+  pa.surrogate = surrogate ? 1 : 0;
+  return pa;
+}
+
+template <typename T>
+cudaError_t elm_dispatch(st_problem* h, int level, int prec, int tangent, const void* cache, const void* fcache, int mu,
+                         int stride, int slot, void* E, const int* bcells, int nbc) {
+  OpArgs a;
+  fill_op_args(h, level, a);
+  a.tangent = tangent;
+  a.cache = cache;
+  a.fcache = fcache;
+  a.elm_mu = mu;
+  a.elm_stride = stride;
+  a.elm_slot = slot;
+  const Level& L = h->lev[level];
+  return h->dim == 2 ? dispatch_elm_2d(h, L, a, prec, tangent, E, bcells, nbc)
+                     : dispatch_elm_3d(h, L, a, prec, tangent, E, bcells, nbc);
+}
+
+template <typename T>
+cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
+  // y = A_l x
+  const Level& L = h->lev[l];
+  const int prec = sizeof(T) == 8 ? ST_FP64 : ST_FP32;
+  cudaError_t e = cudaMemsetAsync(y, 0, L.Nst * sizeof(T), h->stream);
+  if (e != cudaSuccess) return e;
+  if (l == (int)h->lev.size() - 1) return launch_op(h, l, OP_JAC, prec, h->lin_tangent, x, y, nullptr, nullptr);
+  PatchArgs pa = patch_args(h, l, false);
+  for (int c = 0; c < (1 << h->dim); ++c) {
+    const long ncol = L.col_start[c + 1] - L.col_start[c];
+    if (ncol == 0) continue;
+    const unsigned g = (unsigned)(ncol < 8L * h->nsm ? ncol : 8L * h->nsm);
+    if (h->dim == 2)
+      coarse_apply<2, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, y, L.c0[c][0], L.c0[c][1],
+                                                   L.c0[c][2], L.cn[c][0], L.cn[c][1], ncol, L.Nq2, L.Nq1, L.Mv, L.Mp);
+    else
+      coarse_apply<3, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, y, L.c0[c][0], L.c0[c][1],
+                                                   L.c0[c][2], L.cn[c][0], L.cn[c][1], ncol, L.Nq2, L.Nq1, L.Mv, L.Mp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r, T* d) {
+  const Level& L = h->lev[l];
+  MgLevelData& D = m->L[l];
+  const int N = h->K1 * ne_of(h->dim);
+  for (int s = 0; s < sweeps; ++s) {
+    cudaError_t e = level_apply<T>(h, m, l, d, (T*)D.t2);
+    if (e != cudaSuccess) return e;
+    sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int c = 0; c < (1 << h->dim); ++c) {
+      const long ncol = L.col_start[c + 1] - L.col_start[c];
+      if (ncol == 0) continue;
+      const unsigned g = (unsigned)(ncol < 16L * h->nsm ? ncol : 16L * h->nsm);
+      const int nt = N <= 128 ? 128 : 256;
+      if (h->dim == 2)
+        vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, D.piv, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
+                                                         L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
+                                                         L.cn[c][1], ncol, h->P.omega, L.Nq2, L.Nq1, L.Mv, L.Mp);
+      else
+        vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, D.piv, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
+                                                         L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
+                                                         L.cn[c][1], ncol, h->P.omega, L.Nq2, L.Nq1, L.Mv, L.Mp);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// slab restriction y = P^T x (fine level l -> l-1) or prolongation-add
+// y += P x (l-1 -> l), one 1D pass per direction; w1, w2: fine-size work
+template <typename T>
+cudaError_t transfer(st_problem* h, MgState* m, int l, bool restrict_, const T* x, T* y, T* w1, T* w2) {
+  const Level& F = h->lev[l];
+  const Level& C = h->lev[l - 1];
+  const int d = h->dim, K1 = h->K1;
+  const double* P2 = m->d_tab;
+  const double* P1 = m->d_tab + 15;
+  T* last = nullptr;
+  for (int part = 0; part < 2; ++part) {
+    const int nblk = part == 0 ? K1 * d : K1;
+    const size_t offF = part == 0 ? 0 : (size_t)K1 * F.Mv, offC = part == 0 ? 0 : (size_t)K1 * C.Mv;
+    int g[3];
+    for (int a = 0; a < 3; ++a) g[a] = (int)(restrict_ ? (part == 0 ? F.g2[a] : F.g1[a]) : (part == 0 ? C.g2[a] : C.g1[a]));
+    const T* src = x + (restrict_ ? offF : offC);
+    for (int dir = 0; dir < d; ++dir) {
+      T* work = (dir & 1) ? w2 : w1;
+      T* dst = (restrict_ && dir == d - 1) ? y + offC : work + offF;
+      const int nc = C.n[dir];
+      int go[3] = {g[0], g[1], g[2]};
+      go[dir] = restrict_ ? (part == 0 ? 2 * nc + 1 : nc + 1) : (part == 0 ? 4 * nc + 1 : 2 * nc + 1);
+      const size_t nout = (size_t)go[0] * go[1] * go[2] * nblk;
+      const unsigned gr = gridn(nout, h->nsm);
+      if (restrict_) {
+        if (part == 0) restrict_pass<T, 2><<<gr, 256, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, nc, nblk, P2);
+        else restrict_pass<T, 1><<<gr, 256, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, nc, nblk, P1);
+      } else {
+        if (part == 0) prolong_pass<T, 2><<<gr, 256, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, nc, nblk, P2);
+        else prolong_pass<T, 1><<<gr, 256, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, nc, nblk, P1);
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      g[dir] = go[dir];
+      src = dst;
+      if (dir == d - 1) last = work;
+    }
+  }
+  if (!restrict_) {  // y += P x  (the prolongation sits in `last`)
+    axpy_conv<T, T><<<gridn(F.Nst, h->nsm), 256, 0, h->stream>>>(last, y, F.Nst, 1.0, 1.0);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t vcycle_rec(st_problem* h, MgState* m, int l, const T* r, T* d) {
+  const Level& L = h->lev[l];
+  cudaError_t e = cudaMemsetAsync(d, 0, L.Nst * sizeof(T), h->stream);
+  if (e != cudaSuccess) return e;
+  if (l == 0) return vanka_steps<T>(h, m, 0, h->P.coarse_sweeps, r, d);
+  e = vanka_steps<T>(h, m, l, h->P.pre_smooth, r, d);
+  if (e != cudaSuccess) return e;
+  MgLevelData& D = m->L[l];
+  MgLevelData& Cd = m->L[l - 1];
+  // defect and restriction: r_c = P^T (r - A d)
+  e = level_apply<T>(h, m, l, d, (T*)D.t2);
+  if (e != cudaSuccess) return e;
+  sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = transfer<T>(h, m, l, true, (const T*)D.t, (T*)Cd.r, (T*)D.t2, (T*)D.t3);
+  if (e != cudaSuccess) return e;
+  e = vcycle_rec<T>(h, m, l - 1, (const T*)Cd.r, (T*)Cd.d);
+  if (e != cudaSuccess) return e;
+  e = transfer<T>(h, m, l, false, (const T*)Cd.d, d, (T*)D.t, (T*)D.t2);
+  if (e != cudaSuccess) return e;
+  return vanka_steps<T>(h, m, l, h->P.post_smooth, r, d);
+}
+
+}  // namespace
+
 st_status mg_destroy(st_problem* h) {
-  (void)h;
+  if (h && h->mg) {
+    MgState* m = (MgState*)h->mg;
+    free_mg(m);
+    delete m;
+    h->mg = nullptr;
+  }
   return ST_OK;
 }
+
+st_status mg_setup(st_problem* h, st_prec prec) {
+  if (!h->lin_valid) return set_error(h, ST_EINVAL, "st_precond_setup: no linearisation (call st_linearize)");
+  if (h->d_Ulin == nullptr) return set_error(h, ST_EINVAL, "st_precond_setup: no linearisation state");
+  MgState* m = (MgState*)h->mg;
+  if (!m) {
+    m = new MgState();
+    h->mg = m;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!m->allocated || m->prec != prec) {
+    free_mg(m);
+    e = alloc_mg(h, m, prec);
+    if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup alloc");
+  }
+  const int nl = (int)h->lev.size(), L = nl - 1;
+  const Level& F = h->lev[L];
+  const int NE = ne_of(h->dim), K1 = h->K1, N = K1 * NE;
+  const size_t es = esz(prec);
+  const int tangent = h->lin_tangent;
+  const void* cache = prec == ST_FP64 ? (const void*)h->d_cache64 : (const void*)h->d_cache32;
+  const void* fcache = prec == ST_FP64 ? (const void*)h->d_fcache64 : (const void*)h->d_fcache32;
+  // finest level: exact element matrices per node (for the Galerkin operators)
+  if (nl > 1)
+    for (int mu = 0; mu < K1 && e == cudaSuccess; ++mu)
+      e = prec == ST_FP64 ? elm_dispatch<double>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc)
+                          : elm_dispatch<float>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc);
+  if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup element matrices");
+  // representative state and its coefficients -> surrogate matrices
+  {
+    const double* lr = h->T.lrep;
+    rep_state_kernel<<<gridn(F.Mv + F.Mp, h->nsm), 256, 0, h->stream>>>(
+        h->d_Ulin, m->Urep, K1, F.Mv, (long)K1 * F.Mp, lr[0], K1 > 1 ? lr[1] : 0.0, K1 > 2 ? lr[2] : 0.0,
+        K1 > 3 ? lr[3] : 0.0);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      // linearise at U_rep into the representative caches
+      double* c64 = h->d_cache64;
+      double* f64 = h->d_fcache64;
+      h->d_cache64 = m->cache_rep64;
+      h->d_fcache64 = m->fcache_rep64;
+      e = launch_op(h, L, OP_LIN, ST_FP64, tangent, m->Urep, nullptr, nullptr, nullptr);
+      h->d_cache64 = c64;
+      h->d_fcache64 = f64;
+    }
+    if (e == cudaSuccess && prec == ST_FP32) {
+      e = cast_f64_f32(m->cache_rep64, m->cache_rep32, h->cache_len, h->stream);
+      if (e == cudaSuccess) e = cast_f64_f32(m->fcache_rep64, m->fcache_rep32, h->fcache_len, h->stream);
+    }
+    const void* rc = prec == ST_FP64 ? (const void*)m->cache_rep64 : (const void*)m->cache_rep32;
+    const void* rf = prec == ST_FP64 ? (const void*)m->fcache_rep64 : (const void*)m->fcache_rep32;
+    if (e == cudaSuccess) {
+      e = cudaMemsetAsync(m->Erep, 0, (size_t)F.ncells * NE * NE * es, h->stream);
+    }
+    if (e == cudaSuccess)
+      e = prec == ST_FP64 ? elm_dispatch<double>(h, L, prec, tangent, rc, rf, 0, 1, 0, m->Erep, m->bcells, m->nbc)
+                          : elm_dispatch<float>(h, L, prec, tangent, rc, rf, 0, 1, 0, m->Erep, m->bcells, m->nbc);
+  }
+  if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup surrogate matrices");
+  // Galerkin coarse operators
+  for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
+    const Level& C = h->lev[l];
+    const size_t sm = 3 * (size_t)NE * NE * es;
+    const long items = C.ncells * K1;
+    const unsigned g = (unsigned)(items < 4L * h->nsm ? items : 4L * h->nsm);
+    if (prec == ST_FP64) {
+      if (h->dim == 2) {
+        cudaFuncSetAttribute(galerkin_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_kernel<2, double><<<g, 256, sm, h->stream>>>((const double*)m->L[l + 1].E, (double*)m->L[l].E,
+                                                              C.n[0], C.n[1], 1, K1, m->d_pch);
+      } else {
+        cudaFuncSetAttribute(galerkin_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_kernel<3, double><<<g, 256, sm, h->stream>>>((const double*)m->L[l + 1].E, (double*)m->L[l].E,
+                                                              C.n[0], C.n[1], C.n[2], K1, m->d_pch);
+      }
+    } else {
+      if (h->dim == 2) {
+        cudaFuncSetAttribute(galerkin_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_kernel<2, float><<<g, 256, sm, h->stream>>>((const float*)m->L[l + 1].E, (float*)m->L[l].E, C.n[0],
+                                                             C.n[1], 1, K1, m->d_pch);
+      } else {
+        cudaFuncSetAttribute(galerkin_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_kernel<3, float><<<g, 256, sm, h->stream>>>((const float*)m->L[l + 1].E, (float*)m->L[l].E, C.n[0],
+                                                             C.n[1], C.n[2], K1, m->d_pch);
+      }
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup Galerkin");
+  // patches: assemble + factorise
+  e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+  for (int l = 0; l < nl && e == cudaSuccess; ++l) {
+    const Level& Lv = h->lev[l];
+    const bool sur = (l == L);
+    PatchArgs pa = patch_args(h, l, sur);
+    const void* Esrc = sur ? m->Erep : m->L[l].E;
+    const int estride = sur ? 1 : K1;
+    const unsigned g = (unsigned)(Lv.ncells < 8L * h->nsm ? Lv.ncells : 8L * h->nsm);
+    if (prec == ST_FP64) {
+      if (h->dim == 2) patch_assemble<2, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
+      else patch_assemble<3, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        lu_kernel<double><<<g, 256, 0, h->stream>>>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
+    } else {
+      if (h->dim == 2) patch_assemble<2, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
+      else patch_assemble<3, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        lu_kernel<float><<<g, 256, 0, h->stream>>>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup patches");
+  int flag = 0;
+  e = cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup");
+  if (flag) return set_error(h, ST_SINGULAR_PATCH, "st_precond_setup: a patch matrix has a zero pivot");
+  h->precond_valid = true;
+  h->precond_prec = prec;
+  return ST_OK;
+}
+
+st_status mg_vanka(st_problem* h, int level, int sweeps, st_prec prec, const void* r, void* d) {
+  MgState* m = (MgState*)h->mg;
+  cudaError_t e = prec == ST_FP64 ? vanka_steps<double>(h, m, level, sweeps, (const double*)r, (double*)d)
+                                  : vanka_steps<float>(h, m, level, sweeps, (const float*)r, (float*)d);
+  return cuda_check(h, e, "st_vanka_smooth");
+}
+
+st_status mg_vcycle(st_problem* h, st_prec prec, const void* r, void* d) {
+  MgState* m = (MgState*)h->mg;
+  const int L = (int)h->lev.size() - 1;
+  cudaError_t e = prec == ST_FP64 ? vcycle_rec<double>(h, m, L, (const double*)r, (double*)d)
+                                  : vcycle_rec<float>(h, m, L, (const float*)r, (float*)d);
+  return cuda_check(h, e, "st_vcycle");
+}
+
 }  // namespace st
 
 using namespace st;
 
 extern "C" {
+
 st_status st_precond_setup(st_problem* h, st_prec prec) {
-  (void)prec;
-  return set_error(h, ST_EINVAL, "st_precond_setup: not available yet");
+  if (!h) return ST_EINVAL;
+  if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_precond_setup: bad precision");
+  return mg_setup(h, prec);
 }
+
 st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, const void* r, void* d) {
-  (void)level; (void)sweeps; (void)prec; (void)r; (void)d;
-  return set_error(h, ST_EINVAL, "st_vanka_smooth: not available yet");
+  if (!h) return ST_EINVAL;
+  if (level < 0 || level >= (int)h->lev.size()) return set_error(h, ST_EINVAL, "st_vanka_smooth: bad level");
+  if (sweeps < 0 || !r || !d) return set_error(h, ST_EINVAL, "st_vanka_smooth: bad arguments");
+  if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_vanka_smooth: bad precision");
+  if (!h->precond_valid || h->precond_prec != prec) {
+    st_status s = mg_setup(h, prec);
+    if (s != ST_OK) return s;
+  }
+  return mg_vanka(h, level, sweeps, prec, r, d);
 }
+
 st_status st_vcycle(st_problem* h, st_prec prec, const void* r, void* d) {
-  (void)prec; (void)r; (void)d;
-  return set_error(h, ST_EINVAL, "st_vcycle: not available yet");
+  if (!h) return ST_EINVAL;
+  if (!r || !d) return set_error(h, ST_EINVAL, "st_vcycle: r and d are required");
+  if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_vcycle: bad precision");
+  if (!h->precond_valid || h->precond_prec != prec) {
+    st_status s = mg_setup(h, prec);
+    if (s != ST_OK) return s;
+  }
+  return mg_vcycle(h, prec, r, d);
 }
-st_status st_newton_step(st_problem* h, st_tangent tangent, st_prec vcycle_prec, void* U, const void* v_prev,
-                         const void* f, st_newton_info* info) {
-  (void)tangent; (void)vcycle_prec; (void)U; (void)v_prev; (void)f; (void)info;
-  return set_error(h, ST_EINVAL, "st_newton_step: not available yet");
-}
-}
+
+}  // extern "C"

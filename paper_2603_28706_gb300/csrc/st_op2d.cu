@@ -5,6 +5,10 @@ namespace st {
 cudaError_t dispatch_op_2d(const st_problem* h, const Level& L, OpArgs& a, int mode, int prec, int tangent) {
   return dispatch_op_dim<2>(h, L, a, mode, prec, tangent);
 }
+cudaError_t dispatch_elm_2d(const st_problem* h, const Level& L, const OpArgs& a, int prec, int tangent, void* E,
+                           const int* bcells, int nbc) {
+  return dispatch_elm_dim<2>(h, L, a, prec, tangent, E, bcells, nbc);
+}
 cudaError_t upload_consts_2d(const ConstTables& t, const ConstTablesF& tf) {
   cudaError_t e = cudaMemcpyToSymbol(cT, &t, sizeof(t));
   if (e != cudaSuccess) return e;

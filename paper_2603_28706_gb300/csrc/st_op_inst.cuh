@@ -104,4 +104,59 @@ cudaError_t dispatch_op_dim(const st_problem* h, const Level& L, OpArgs& a, int 
   return cudaErrorInvalidValue;
 }
 
+
+// Spatial element matrices (times tau w_mu) of every cell at node mu from the
+// coefficient caches in a.cache / a.fcache: volume part by probing the
+// sum-factorised element operator with unit vectors (one column per slot),
+// boundary-face part added by st_face_matrix.  E: [ncells][K1][NE][NE].
+template <int DIM, int K1, typename T, int TAN>
+cudaError_t launch_elm_t(const st_problem* h, const Level& L, OpArgs a, T* E, const int* bcells, int nbc) {
+  using Cfg = OpCfg<DIM, K1, T>;
+  using FCfg = FaceCfg<DIM, T>;
+  auto kern = st_op_kernel<DIM, K1, T, OP_ELM, TAN>;
+  auto fkern = st_face_matrix<DIM, K1, T, TAN>;
+  constexpr int NE = Dims<DIM>::NE;
+  const size_t fsm = (size_t)NE * FCfg::per_slot * sizeof(T) + 64;
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::NT, Cfg::smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  a.out = E;
+  a.ncol = L.ncells * NE;
+  a.col_start = 0;
+  long grid = (a.ncol + Cfg::S - 1) / Cfg::S;
+  if (grid > (long)occ * h->nsm) grid = (long)occ * h->nsm;
+  kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nbc == 0) return e;
+  long fg = nbc < 4L * h->nsm ? nbc : 4L * h->nsm;
+  fkern<<<(unsigned)fg, OP_THREADS, fsm, h->stream>>>(a, bcells, nbc, E);
+  return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t dispatch_elm_dim(const st_problem* h, const Level& L, const OpArgs& a, int prec, int tangent, void* E,
+                             const int* bcells, int nbc) {
+  const bool r1 = tangent != ST_PIC;
+#define ST_ELM_CASE(K)                                                                                            \
+  case K:                                                                                                         \
+    if (prec == ST_FP64)                                                                                          \
+      return r1 ? launch_elm_t<DIM, K, double, 1>(h, L, a, (double*)E, bcells, nbc)                                \
+                : launch_elm_t<DIM, K, double, 0>(h, L, a, (double*)E, bcells, nbc);                               \
+    return r1 ? launch_elm_t<DIM, K, float, 1>(h, L, a, (float*)E, bcells, nbc)                                    \
+              : launch_elm_t<DIM, K, float, 0>(h, L, a, (float*)E, bcells, nbc);
+  switch (h->K1) {
+    ST_ELM_CASE(1)
+    ST_ELM_CASE(2)
+    ST_ELM_CASE(3)
+    ST_ELM_CASE(4)
+  }
+#undef ST_ELM_CASE
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace st

@@ -206,6 +206,14 @@ __device__ __forceinline__ void rpass_acc(T* acc, const MT* m, const T* g) {
   }
 }
 
+// colour-ordered index of a linear cell id (the coefficient caches use it)
+template <int DIM>
+__device__ __forceinline__ long colour_index(const OpArgs& a, int cell) {
+  const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+  const int c = (ex & 1) | ((ey & 1) << 1) | ((ez & 1) << 2);
+  return a.col_start_all[c] + (ex >> 1) + (long)a.cn_all[c][0] * ((ey >> 1) + (long)a.cn_all[c][1] * (ez >> 1));
+}
+
 template <int DIM, int K1, typename T>
 struct OpCfg {
   using D = Dims<DIM>;
@@ -219,7 +227,7 @@ struct OpCfg {
   static constexpr int SP = D::NP;
   static constexpr int SQ = D::NQ;
   static constexpr int per_slot = SX + SG + SP + SQ;
-  static constexpr size_t smem_bytes = (size_t)S * per_slot * sizeof(T) + (size_t)C * sizeof(int) + 64;
+  static constexpr size_t smem_bytes = (size_t)S * per_slot * sizeof(T) + (size_t)S * sizeof(int) + 64;
 };
 
 template <int DIM, int K1, typename T, int MODE, int TAN>
@@ -255,18 +263,24 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
   }
   __syncthreads();
 
-  for (long b0 = cbeg; b0 < cend; b0 += C) {
-    const int nc = (int)min((long)C, cend - b0);
-    const int ns = nc * K1;
+  constexpr int SK = (MODE == OP_ELM) ? 1 : K1;  // slots per batch item
+  constexpr int CB = (MODE == OP_ELM) ? S : C;    // items per batch
+  for (long b0 = cbeg; b0 < cend; b0 += CB) {
+    const int nc = (int)min((long)CB, cend - b0);
+    const int ns = nc * SK;
 
-    // ---- batch setup: cell ids
+    // ---- batch setup: cell ids (element-matrix mode: item = (cell, column))
     for (int ci = threadIdx.x; ci < nc; ci += blockDim.x) {
-      const long li = b0 + ci;  // index within the colour class
-      const int i = (int)(li % a.cn[0]);
-      const int j = (int)((li / a.cn[0]) % a.cn[1]);
-      const int l = (int)(li / ((long)a.cn[0] * a.cn[1]));
-      const int ex = a.c0[0] + 2 * i, ey = a.c0[1] + 2 * j, ez = (DIM == 3) ? a.c0[2] + 2 * l : 0;
-      sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
+      if constexpr (MODE == OP_ELM) {
+        sCell[ci] = (int)((b0 + ci) / D::NE);
+      } else {
+        const long li = b0 + ci;  // index within the colour class
+        const int i = (int)(li % a.cn[0]);
+        const int j = (int)((li / a.cn[0]) % a.cn[1]);
+        const int l = (int)(li / ((long)a.cn[0] * a.cn[1]));
+        const int ex = a.c0[0] + 2 * i, ey = a.c0[1] + 2 * j, ez = (DIM == 3) ? a.c0[2] + 2 * l : 0;
+        sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
+      }
     }
     __syncthreads();
 
@@ -275,6 +289,14 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
     //      prefetch the batch's coefficient-cache block into L2 meanwhile
     for (int it = threadIdx.x; it < ns * (NC * NQ + NP); it += blockDim.x) {
       const int s = it / (NC * NQ + NP), r = it % (NC * NQ + NP);
+      if constexpr (MODE == OP_ELM) {
+        // unit vector e_j of the cell's local dofs (velocity c-major, then pressure)
+        const int jcol = (int)((b0 + s) % D::NE);
+        const T v = (r == jcol) ? (T)1 : (T)0;
+        if (r < NC * NQ) sX[s * Cfg::SX + r] = v;
+        else sP[s * NP + (r - NC * NQ)] = v;
+        continue;
+      }
       const int ci = s / K1, mu = s % K1;
       const int cell = sCell[ci];
       const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
@@ -329,8 +351,8 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
     // ---- S3: pointwise work at every quadrature point of every slot
     for (int it = threadIdx.x; it < ns * NQ; it += blockDim.x) {
       const int s = it / NQ, q = it % NQ;
-      const int ci = s / K1, mu = s % K1;
-      const long gidx = a.col_start + b0 + ci;  // colour-ordered cell index
+      const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
+      const long gidx = (MODE == OP_ELM) ? colour_index<DIM>(a, sCell[ci]) : a.col_start + b0 + ci;  // colour-ordered cell index
       T u[3] = {0, 0, 0}, g[3][3];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -371,7 +393,7 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
         for (int i = 0; i < NS; ++i) cp[(2 + i) * NQ] = A[i];
 #pragma unroll
         for (int c = 0; c < NC; ++c) cp[(2 + NS + c) * NQ] = -(double)u[c] * tw;
-      } else if constexpr (MODE == OP_JAC) {
+      } else if constexpr (MODE == OP_JAC || MODE == OP_ELM) {
         const T* cp = reinterpret_cast<const T*>(a.cache) + ((gidx * K1 + mu) * (long)D::NF_VOL) * NQ + q;
         const T etaw = cp[0];
         T nuw[3] = {0, 0, 0};
@@ -475,7 +497,7 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
       for (int it = threadIdx.x; it < ns * (NC + NP); it += blockDim.x) {
         if (it < ns * NC) {
           const int s = it / NC, c = it % NC;
-          const int ci = s / K1, mu = s % K1;
+          const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
           T acc[NQ];
           if constexpr (MODE == OP_JAC) {
             // tv_mu(q) = W(q) sum_j (K_t vol)_{mu j} du_j(q)
@@ -520,6 +542,14 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
 #pragma unroll
             for (int q = 0; q < NQ; ++q) acc[q] += y[q];
           }
+          if constexpr (MODE == OP_ELM) {
+            // column j of the element matrix (rows: velocity c-major, then pressure)
+            const long item = b0 + s;
+            T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) E[(long)(c * NQ + q) * D::NE] = acc[q];
+            continue;
+          }
           // scatter-add (cells of one colour class share no node): all loads
           // first so that they are in flight together, then the stores
           T* ob = out + (long)mu * a.Mv + c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
@@ -536,12 +566,18 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
         } else {
           const int r = it - ns * NC;
           const int s = r / NP, m = r % NP;
-          const int ci = s / K1, mu = s % K1;
+          const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
           T acc = 0;
 #pragma unroll
           for (int q = 0; q < NQ; ++q) acc += ((DIM == 3) ? ct.PSI3[q * 8 + m] : ct.PSI2[q * 4 + m]) * sQ[s * NQ + q];
           const int cell = sCell[ci];
           const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+          if constexpr (MODE == OP_ELM) {
+            const long item = b0 + s;
+            T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
+            E[(long)(NC * NQ + m) * D::NE] = acc;
+            continue;
+          }
           const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
           const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
           out[(long)K1 * a.Mv + (long)mu * a.Mp + g] += acc;

@@ -1,0 +1,100 @@
+"""Parity of the CUDA Vanka smoother and V-cycle (st_vanka_smooth, st_vcycle)
+with the oracle hierarchy (Sec. 6.3).  FP64: max|gpu - oracle| <= 1e-9
+max|oracle| (patch LUs pivot in the same order; sums differ in rounding).
+FP32: <= 1e-3 max|oracle|: a single-precision LU solve is accurate to about
+kappa(A_K) * 6e-8 and the saddle-point patches have kappa ~ 1e4; the
+normwise backward error of the patch solves is checked separately."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mg as mg
+import st_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-9, 1e-3
+VAR = {0: oracle.PIC, 1: oracle.EXN, 2: oracle.MODN}
+
+
+def gpu():
+    import paper_2603_28706_gb300 as st
+    return st
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def rel(g, ref):
+    return np.abs(g.detach().double().cpu().numpy() - ref).max() / np.abs(ref).max()
+
+
+def smooth_state(p, seed=0):
+    return si.fourier_state(p, seed)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("tg", [1, 2])
+def test_single_patch_vanka(dim, tg):
+    p = si.base_params(dim=dim, nx=1, ny=1, nz=1, k=1, p=1.4, delta=0.1, nu=0.3, nu_inf=0.05, sigma_max=0.1,
+                       omega=1.0, levels=1)
+    st = gpu()
+    U = smooth_state(p)
+    r = si.uniform(oracle.sizes(p)["Nst"], 1)
+    H = mg.Hierarchy(p, VAR[tg], U, 1, 1.0, 1, 1, coarse_sweeps=1)
+    ref = H.vanka_step(0, r, np.zeros_like(r))
+    prob = st.Problem(p)
+    prob.linearize(tg, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        d = torch.zeros(prob.num_dofs(), dtype=dt, device="cuda")
+        prob.vanka_smooth(0, 1, dev(r, dt), d, prec=prec)
+        assert rel(d, ref) <= tol, (prec, rel(d, ref))
+        # normwise backward error |A x - r| / (|A| |x|) of the patch solve (one
+        # patch = the whole surrogate slab operator): a few unit roundoffs
+        At = mg.surrogate_operator(p, VAR[tg], U)
+        x = d.double().cpu().numpy()
+        berr = np.abs(At @ x - r).max() / (abs(At).sum(axis=1).max() * np.abs(x).max())
+        assert berr <= (1e-14 if prec == st.ST_FP64 else 1e-6), berr
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=3, ny=3, k=1), dict(dim=2, nx=4, ny=2, k=2, inflow_profile=1),
+                                  dict(dim=3, nx=2, ny=2, nz=2, k=1), dict(dim=3, nx=3, ny=2, nz=2, k=0)])
+def test_vanka_sweeps(case):
+    p = si.base_params(p=1.5, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, levels=1, **case)
+    st = gpu()
+    U = smooth_state(p)
+    s = oracle.sizes(p)
+    r = si.uniform(s["Nst"], 1)
+    d0 = 0.1 * si.uniform(s["Nst"], 2)
+    H = mg.Hierarchy(p, oracle.MODN, U, 1, p["omega"], 1, 1)
+    ref = H.smooth(0, r, d0.copy(), 2)
+    prob = st.Problem(p)
+    prob.linearize(st.ST_MODN, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        d = dev(d0, dt)
+        prob.vanka_smooth(0, 2, dev(r, dt), d, prec=prec)
+        assert rel(d, ref) <= tol, (prec, rel(d, ref))
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=4, ny=4, k=1, levels=2),
+                                  dict(dim=2, nx=8, ny=4, k=2, levels=3, inflow_profile=1),
+                                  dict(dim=3, nx=4, ny=4, nz=4, k=1, levels=3),
+                                  dict(dim=3, nx=4, ny=2, nz=2, k=2, levels=2)])
+def test_vcycle(case):
+    p = si.base_params(p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, coarse_sweeps=4, **case)
+    st = gpu()
+    U = smooth_state(p)
+    s = oracle.sizes(p)
+    r = si.uniform(s["Nst"], 1)
+    for tg in (1, 2):
+        H = mg.Hierarchy(p, VAR[tg], U, p["levels"], p["omega"], p["pre_smooth"], p["post_smooth"],
+                         coarse_sweeps=p["coarse_sweeps"])
+        ref = H.vcycle(r)
+        prob = st.Problem(p)
+        prob.linearize(tg, dev(U))
+        for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+            d = prob.vcycle(dev(r, dt), prec=prec)
+            assert rel(d, ref) <= tol, (tg, prec, rel(d, ref))
+        prob.close()
