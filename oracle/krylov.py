@@ -10,8 +10,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain numpy loops:
   newton        globalised Newton-type iteration on one slab (Sec. 4.1, 6.2):
                 inexact solve to the Eisenstat-Walker forcing (choice 2),
                 Armijo backtracking on phi = 1/2 |R|_M^2 for exN/modN,
-                lambda = 1 for Pic, stop by eq. nk-stop, preconditioner
-                refresh rule of Sec. 6.3
+                lambda = 1 for Pic, stop by eq. nk-stop; the finest-level
+                surrogate patches follow the refresh rule of Sec. 6.3, the
+                operator and the coarse levels follow every iterate
 """
 import numpy as np
 import scipy.sparse as sp
@@ -101,9 +102,11 @@ def newton(p, var, U0, vprev, f=None, vcycle_levels=1, max_iter=30, tol_abs=1e-1
         J = assemble_csr(p, var, U)
         rebuild = H is None or (prev_ratio is not None and prev_ratio > rho) or \
             (len(lin_its) >= 2 and lin_its[-1] > 2 * lin_its[-2])
-        if rebuild:
+        if H is None:
             H = mg.Hierarchy(p, var, U, vcycle_levels, omega, pre, post, coarse_sweeps)
-            rebuilds += 1
+        else:
+            H.update(var, U, rebuild_finest=rebuild)
+        rebuilds += int(rebuild)
         if var == PIC:
             forcing = lin_rtol
         else:
@@ -114,8 +117,10 @@ def newton(p, var, U0, vprev, f=None, vcycle_levels=1, max_iter=30, tol_abs=1e-1
                     e_new = max(e_new, safeguard)
                 eta = min(ew_max, e_new)
             forcing = eta
-        dU, its, _ = fgmres(lambda x: J @ x, R, H.vcycle, M, forcing, restart, maxit)
+        dU, its, lres = fgmres(lambda x: J @ x, R, H.vcycle, M, forcing, restart, maxit)
         lin_its.append(its)
+        if lres > forcing * rn * (1 + 1e-12):  # the linear solve missed its tolerance (Sec. 6.2)
+            return U, dict(status="linear_failed", iters=m, hist=hist, lin_its=lin_its, rebuilds=rebuilds)
         lam = 1.0
         while True:
             Un = U + lam * dU

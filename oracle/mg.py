@@ -115,28 +115,37 @@ def surrogate_operator(p, var, U):
 
 
 class Hierarchy:
-    """Levels 0 (coarsest) .. L (finest) with operators and patch inverses."""
+    """Levels 0 (coarsest) .. L (finest) with operators and patch inverses.
+
+    update() re-linearises: the finest operator A_L = J_n(U), the Galerkin
+    coarse operators and their exact patches always follow the current
+    iterate; the finest-level surrogate patches are rebuilt only when asked
+    (the refresh rule of Sec. 6.3 keeps them otherwise)."""
 
     def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True):
-        self.levels = levels
+        self.p, self.levels = p, levels
         self.omega = omega
         self.pre, self.post, self.coarse_sweeps = pre, post, coarse_sweeps
+        self.surrogate = surrogate
         self.params = [coarse_params(p, levels - 1 - l) for l in range(levels)]
-        self.A = [None] * levels
         self.P = [None] * levels  # P[l]: level l-1 -> level l
-        self.A[-1] = assemble_csr(p, var, U)
         for l in range(levels - 1, 0, -1):
             self.P[l] = prolongation(self.params[l - 1])
+        self.dofs = [cell_dofs(pl, np.arange(sizes(pl)["ncells"])) for pl in self.params]
+        self.A = [None] * levels
+        self.Ainv = [None] * levels
+        self.update(var, U, rebuild_finest=True)
+
+    def update(self, var, U, rebuild_finest):
+        L = self.levels - 1
+        self.A[L] = assemble_csr(self.p, var, U)
+        for l in range(L, 0, -1):
             self.A[l - 1] = galerkin(self.A[l], self.P[l])
-        self.Ainv = []
-        self.dofs = []
-        for l in range(levels):
-            pl = self.params[l]
-            ncell = sizes(pl)["ncells"]
-            D = cell_dofs(pl, np.arange(ncell))
-            src = surrogate_operator(p, var, U) if (l == levels - 1 and surrogate) else self.A[l]
-            self.dofs.append(D)
-            self.Ainv.append([np.linalg.inv(exact_patch(src, D[c])) for c in range(ncell)])
+        for l in range(self.levels):
+            if l == L and not rebuild_finest and self.Ainv[L] is not None:
+                continue
+            src = surrogate_operator(self.p, var, U) if (l == L and self.surrogate) else self.A[l]
+            self.Ainv[l] = [np.linalg.inv(exact_patch(src, dof)) for dof in self.dofs[l]]
 
     def vanka_step(self, l, r, d):
         A = self.A[l]

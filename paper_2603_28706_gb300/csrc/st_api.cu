@@ -16,6 +16,7 @@ cudaError_t dispatch_op_3d(const st_problem* h, const Level& L, OpArgs& a, int m
 cudaError_t upload_consts_2d(const ConstTables& t, const ConstTablesF& tf);
 cudaError_t upload_consts_3d(const ConstTables& t, const ConstTablesF& tf);
 st_status mg_destroy(st_problem* h);
+void krylov_destroy(st_problem* h);
 
 st_status set_error(st_problem* h, st_status s, const std::string& msg) {
   if (h) h->last_error = msg;
@@ -398,6 +399,7 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
 st_status st_destroy(st_problem* h) {
   if (!h) return ST_OK;
   mg_destroy(h);
+  krylov_destroy(h);
   for (auto& L : h->lev) {
     cudaFree(L.d_face_off);
     cudaFree(L.d_face_cell);

@@ -145,6 +145,7 @@ struct st_problem {
   bool precond_valid = false;
   int precond_prec = -1;
   void* mg = nullptr;              // multigrid state (st_mg.cu)
+  void* kry = nullptr;             // Krylov / Newton workspace (st_solver.cu)
 };
 
 namespace st {
@@ -155,6 +156,8 @@ cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent,
 void fill_op_args(const st_problem* h, int level, OpArgs& a);
 
 st_status set_error(st_problem* h, st_status s, const std::string& msg);
+st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest);
+st_status mg_vcycle(st_problem* h, st_prec prec, const void* r, void* d);
 st_status cuda_check(st_problem* h, cudaError_t e, const char* where);
 
 }  // namespace st

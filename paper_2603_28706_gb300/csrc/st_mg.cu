@@ -775,7 +775,7 @@ st_status mg_destroy(st_problem* h) {
   return ST_OK;
 }
 
-st_status mg_setup(st_problem* h, st_prec prec) {
+st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
   if (!h->lin_valid) return set_error(h, ST_EINVAL, "st_precond_setup: no linearisation (call st_linearize)");
   if (h->d_Ulin == nullptr) return set_error(h, ST_EINVAL, "st_precond_setup: no linearisation state");
   MgState* m = (MgState*)h->mg;
@@ -788,7 +788,9 @@ st_status mg_setup(st_problem* h, st_prec prec) {
     free_mg(m);
     e = alloc_mg(h, m, prec);
     if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup alloc");
+    rebuild_finest = true;
   }
+  if (!h->precond_valid) rebuild_finest = true;
   const int nl = (int)h->lev.size(), L = nl - 1;
   const Level& F = h->lev[L];
   const int NE = ne_of(h->dim), K1 = h->K1, N = K1 * NE;
@@ -803,7 +805,7 @@ st_status mg_setup(st_problem* h, st_prec prec) {
                           : elm_dispatch<float>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc);
   if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup element matrices");
   // representative state and its coefficients -> surrogate matrices
-  {
+  if (rebuild_finest) {
     const double* lr = h->T.lrep;
     rep_state_kernel<<<gridn(F.Mv + F.Mp, h->nsm), 256, 0, h->stream>>>(
         h->d_Ulin, m->Urep, K1, F.Mv, (long)K1 * F.Mp, lr[0], K1 > 1 ? lr[1] : 0.0, K1 > 2 ? lr[2] : 0.0,
@@ -868,6 +870,7 @@ st_status mg_setup(st_problem* h, st_prec prec) {
   for (int l = 0; l < nl && e == cudaSuccess; ++l) {
     const Level& Lv = h->lev[l];
     const bool sur = (l == L);
+    if (sur && !rebuild_finest) continue;  // refresh rule: keep the surrogate factorisations
     PatchArgs pa = patch_args(h, l, sur);
     const void* Esrc = sur ? m->Erep : m->L[l].E;
     const int estride = sur ? 1 : K1;
@@ -922,7 +925,7 @@ extern "C" {
 st_status st_precond_setup(st_problem* h, st_prec prec) {
   if (!h) return ST_EINVAL;
   if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_precond_setup: bad precision");
-  return mg_setup(h, prec);
+  return mg_setup(h, prec, true);
 }
 
 st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, const void* r, void* d) {
@@ -931,7 +934,7 @@ st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, co
   if (sweeps < 0 || !r || !d) return set_error(h, ST_EINVAL, "st_vanka_smooth: bad arguments");
   if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_vanka_smooth: bad precision");
   if (!h->precond_valid || h->precond_prec != prec) {
-    st_status s = mg_setup(h, prec);
+    st_status s = mg_setup(h, prec, true);
     if (s != ST_OK) return s;
   }
   return mg_vanka(h, level, sweeps, prec, r, d);
@@ -942,7 +945,7 @@ st_status st_vcycle(st_problem* h, st_prec prec, const void* r, void* d) {
   if (!r || !d) return set_error(h, ST_EINVAL, "st_vcycle: r and d are required");
   if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_vcycle: bad precision");
   if (!h->precond_valid || h->precond_prec != prec) {
-    st_status s = mg_setup(h, prec);
+    st_status s = mg_setup(h, prec, true);
     if (s != ST_OK) return s;
   }
   return mg_vcycle(h, prec, r, d);

@@ -1,0 +1,83 @@
+"""GPU Newton step (st_newton_step: FGMRES + V-cycle + Armijo + Eisenstat-Walker)
+against the oracle Newton (Sec. 4.1, 6.1-6.3).  Iteration counts are
+rounding-dependent and only reported; the converged slab solutions must agree
+to the tolerance the stopping rule implies."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.krylov as kr
+import st_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gpu():
+    import paper_2603_28706_gb300 as st
+    return st
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float64)
+
+
+def problem(dim):
+    if dim == 2:
+        return si.base_params(dim=2, nx=4, ny=4, k=1, dt=0.05, p=1.5, delta=0.1, nu=0.1, nu_inf=0.01,
+                              sigma_max=0.02, levels=2, inflow_profile=1, tol_rel=1e-10, tol_abs=1e-14,
+                              coarse_sweeps=4, newton_maxit=40)
+    return si.base_params(dim=3, nx=4, ny=4, nz=4, k=1, dt=0.05, p=1.4, delta=0.1, nu=0.1, nu_inf=0.01,
+                          sigma_max=0.02, levels=2, inflow_profile=1, tol_rel=1e-10, tol_abs=1e-14,
+                          coarse_sweeps=4, newton_maxit=40)
+
+
+def start(p):
+    s = oracle.sizes(p)
+    vprev = 0.3 * si.fourier_velocity(p, 3)[0].reshape(-1)
+    U0 = np.concatenate([vprev] * (p["k"] + 1) + [np.zeros((p["k"] + 1) * s["Mp"])])
+    return U0, vprev
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("tg", [2, 1, 0])
+def test_newton_matches_oracle(dim, tg):
+    st = gpu()
+    p = problem(dim)
+    U0, vprev = start(p)
+    var = {0: oracle.PIC, 1: oracle.EXN, 2: oracle.MODN}[tg]
+    Uo, info = kr.newton(p, var, U0, vprev, vcycle_levels=p["levels"], max_iter=40, tol_rel=p["tol_rel"],
+                         tol_abs=p["tol_abs"], omega=p["omega"], coarse_sweeps=p["coarse_sweeps"])
+    assert info["status"] == "ok"
+    prob = st.Problem(p)
+    for prec in (st.ST_FP64, st.ST_FP32):
+        U = dev(U0)
+        status, ginfo = prob.newton_step(tg, U, dev(vprev), vcycle_prec=prec)
+        assert status == st.ST_OK
+        assert ginfo["res_norm_final"] <= p["tol_rel"] * ginfo["res_norm_initial"] * (1 + 1e-9) or \
+            ginfo["res_norm_final"] <= p["tol_abs"]
+        err = np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+        assert err <= 1e-8, (prec, err, ginfo, info["iters"])
+        # the oracle's residual at the GPU solution is small too
+        Rg = oracle.residual(p, U.cpu().numpy(), vprev=vprev)
+        assert np.sqrt(oracle.mnorm2(p, Rg)) <= 1e-8 * info["hist"][0]
+
+
+def test_newton_failure_paths_keep_handle_usable():
+    st = gpu()
+    p = problem(2)
+    U0, vprev = start(p)
+    # linear solver budget too small: the step is declared unsuccessful
+    pf = dict(p, fgmres_maxit=1, newton_maxit=5)
+    prob = st.Problem(pf)
+    status, info = prob.newton_step(st.ST_MODN, dev(U0), dev(vprev), raise_on_fail=False)
+    assert status == st.ST_NOT_CONVERGED
+    # Armijo with c = 1/2 and lambda_min = 1 cannot accept an inexact step
+    pl = dict(p, armijo_c=0.5, lambda_min=1.0)
+    prob2 = st.Problem(pl)
+    status, info = prob2.newton_step(st.ST_EXN, dev(U0), dev(vprev), raise_on_fail=False)
+    assert status == st.ST_LINESEARCH_FAILED
+    # the handles stay usable
+    status, info = st.Problem(p).newton_step(st.ST_MODN, dev(U0), dev(vprev))
+    assert status == st.ST_OK
+    prob.residual(dev(U0), dev(vprev))
