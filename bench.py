@@ -246,7 +246,7 @@ def main():
         except (OSError, ValueError):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "st_op_kernel<3,2,double,OP_JAC,1> (8 colour launches per apply)",
+                "traffic": traffic, "kernel": "st_op_kernel<3,2,double,OP_JAC,1> (8 colour launches) + st_face_kernel + st_face_gather per apply",
                 "apply_ms": apply_ms, "flops_per_apply": fl, "algorithmic_bytes_per_apply": bytes_per_apply(p),
                 "hbm_frac_of_measured": bytes_per_apply(p) / (apply_ms * 1e-3) / 6771.1e9}
 
@@ -282,8 +282,10 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d random cells of the 32^3 mesh (element matrices formed and applied), Pic+exN+modN, "
                          "%.1f s" % (sample, dt)}
+    # per apply: 8 colour launches of the volume kernel + 1 face kernel + 1 face gather;
+    # per linearisation: 8 volume + 1 face + 2 precision casts
     ncol = 8
-    launches_per_step = len(tangents) * ((ncol + 2) + APPLIES * ncol)
+    launches_per_step = len(tangents) * ((ncol + 1 + 2) + APPLIES * (ncol + 2))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
