@@ -185,6 +185,23 @@ st_status st_newton_step(st_problem* h, st_tangent tangent, st_prec vcycle_prec,
 /* Message describing the last failure on h (never NULL). */
 const char* st_last_error(const st_problem* h);
 
+/* Allocation-free variant of st_mnorm.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (a memory
+ * pool owned by another framework with a hard cap, a plugin host that forbids
+ * device allocations, a latency-critical path that must not touch the
+ * allocator).  It needs no handle: params gives the mesh, k and dt; r is an
+ * FP64 finest-level slab vector (device pointer, caller-owned) and *out (host)
+ * receives |r|_M, the block mass norm of Sec. 6.1.  The work vectors and
+ * partial sums live in a static device array of 16 MiB that every GPU loading
+ * the library holds until exit, so the slab may have at most
+ * (2^21 - 2048) / 2 = 1 047 552 dofs; larger slabs give ST_EINVAL with a
+ * message on stderr.  The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The call calls no cudaMalloc or cudaFree
+ * and synchronises `cuda_stream`.  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+st_status st_mnorm_noalloc(const st_params* params, void* cuda_stream, const double* r, double* out);
+
 #ifdef __cplusplus
 }
 #endif

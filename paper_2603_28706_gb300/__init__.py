@@ -19,7 +19,8 @@ STATUS = {0: "ST_OK", 1: "ST_EINVAL", 2: "ST_ECUDA", 3: "ST_ENOMEM", 4: "ST_NOT_
           5: "ST_LINESEARCH_FAILED", 6: "ST_SINGULAR_PATCH", 7: "ST_DEVICE_TIMEOUT"}
 
 EXPORTED = ["st_setup_mesh", "st_destroy", "st_num_dofs", "st_residual", "st_linearize", "st_jacobian_apply",
-            "st_mnorm", "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step", "st_last_error"]
+            "st_mnorm", "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step", "st_last_error",
+            "st_mnorm_noalloc"]
 
 
 class StParams(ctypes.Structure):
@@ -85,6 +86,8 @@ def load(build_if_missing=True):
     lib.st_newton_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(StNewtonInfo)]
     lib.st_last_error.argtypes = [vp]
     lib.st_last_error.restype = ctypes.c_char_p
+    lib.st_mnorm_noalloc.argtypes = [P, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.st_mnorm_noalloc.restype = ctypes.c_int
     for name in EXPORTED:
         getattr(lib, name)
     for name in ("st_setup_mesh", "st_destroy", "st_residual", "st_linearize", "st_jacobian_apply", "st_mnorm",
@@ -116,6 +119,25 @@ def _ptr(t, dtype=None, n=None, name="vector"):
 def _prec_dtype(prec):
     import torch
     return torch.float64 if prec == ST_FP64 else torch.float32
+
+
+def mnorm_noalloc(p, r, stream=None):
+    """|r|_M without a handle and without any device allocation (st_mnorm_noalloc).
+
+    For callers that cannot allocate device memory; the library keeps a static
+    16 MiB scratch array per GPU, which limits the slab to 1 047 552 dofs.
+    Calls that overlap on the GPU share that array and must be serialised."""
+    import torch
+    lib = load()
+    P = params(p)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    v = ctypes.c_double()
+    st = lib.st_mnorm_noalloc(ctypes.byref(P), ctypes.c_void_p(stream.cuda_stream),
+                              _ptr(r, torch.float64, None, "r"), ctypes.byref(v))
+    if st != ST_OK:
+        raise StError(st, "st_mnorm_noalloc failed (see stderr)")
+    return v.value
 
 
 class Problem:

@@ -1,4 +1,7 @@
 // Vector kernels (see st_blas.cuh).
+#include <cmath>
+#include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "st_blas.cuh"
@@ -249,3 +252,136 @@ cudaError_t mnorm2_f64(st_problem* h, int level, const double* r, double* out) {
 }
 
 }  // namespace st
+
+// ----------------------------------------------------------------------------
+// Allocation-free block mass norm (st_mnorm_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs while another framework
+// owns the device memory pool with a hard cap, plugins whose host forbids
+// device allocations, or latency-critical paths that must not touch the
+// allocator.  For them this entry point computes |r|_M without a handle and
+// without any allocation: its work vectors and reduction partial sums live in
+// the file-scope array below, which every GPU that loads the library keeps
+// until the process exits.
+//   scratch[0 .. 8)           tau * w_mu per Radau node (mass scaling)
+//   scratch[8 .. 8 + 512)     partial sums of the dot product
+//   scratch[1024]             the result
+//   scratch[2048 ..)          two work vectors of the slab size
+// The slab size is therefore limited to (ST_NOALLOC_DOUBLES - 2048) / 2.
+// Every entry that a call reads is written earlier in that call, so nothing
+// has to start at zero.  All calls share the array: calls that overlap on the
+// GPU (two streams, or two host threads) race and must be serialised by the
+// caller.
+constexpr size_t ST_NOALLOC_DOUBLES = (size_t)1 << 21;  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[ST_NOALLOC_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};  // device address of the array, per device
+}  // namespace
+
+extern "C" st_status st_mnorm_noalloc(const st_params* P, void* cuda_stream, const double* r, double* out) {
+  using namespace st;
+  if (!P) return ST_EINVAL;
+  const int d = P->dim;
+  if ((d != 2 && d != 3) || P->nx < 1 || P->ny < 1 || (d == 3 && P->nz < 1) || P->k < 0 || P->k >= MAX_K1 ||
+      !(P->dt > 0) || !(P->Lx > 0) || !(P->Ly > 0) || (d == 3 && !(P->Lz > 0))) {
+    fprintf(stderr, "st_mnorm_noalloc: invalid parameters\n");
+    return ST_EINVAL;
+  }
+  const int K1 = P->k + 1;
+  long g2[3], g1[3];
+  double hh[3];
+  const int nn[3] = {P->nx, P->ny, d == 3 ? P->nz : 1};
+  const double Ls[3] = {P->Lx, P->Ly, d == 3 ? P->Lz : 1.0};
+  long Nq2 = 1, Nq1 = 1;
+  for (int a = 0; a < 3; ++a) {
+    const bool act = a < d;
+    g2[a] = act ? 2L * nn[a] + 1 : 1;
+    g1[a] = act ? (long)nn[a] + 1 : 1;
+    hh[a] = act ? Ls[a] / nn[a] : 1.0;
+    Nq2 *= g2[a];
+    Nq1 *= g1[a];
+  }
+  const size_t Mv = (size_t)d * Nq2, Nst = (size_t)K1 * (Mv + Nq1);
+  if (2048 + 2 * Nst > ST_NOALLOC_DOUBLES) {
+    fprintf(stderr,
+            "st_mnorm_noalloc: the slab has %zu dofs; the static scratch holds at most %zu "
+            "(use st_mnorm with a handle)\n",
+            Nst, (ST_NOALLOC_DOUBLES - 2048) / 2);
+    return ST_EINVAL;
+  }
+  if (!r || !out) return ST_EINVAL;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  // set-up: once per device, with that device current
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) return ST_ECUDA;
+  double* scr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        fprintf(stderr, "st_mnorm_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+        return ST_ECUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)ptr;
+    }
+    scr = g_noalloc_ptr[dev];
+  }
+  TimeTab T;
+  if (!make_time_tables(P->k, T)) return ST_EINVAL;
+  RefTables R;
+  make_ref_tables(R);
+  double tw[MAX_K1];
+  for (int i = 0; i < K1; ++i) tw[i] = P->dt * T.w[i];
+  double* bs = scr;
+  double* part = scr + 8;
+  double* res = scr + 1024;
+  double* w1 = scr + 2048;
+  double* w2 = w1 + Nst;
+  e = cudaMemcpyAsync(bs, tw, K1 * sizeof(double), cudaMemcpyHostToDevice, stream);
+  // M r by one 1D mass pass per direction; the result ends in w1 (3D) or w2 (2D)
+  const double* M = R.M1;
+  double* Mr = nullptr;
+  for (int partv = 0; partv < 2 && e == cudaSuccess; ++partv) {
+    const long* g = partv == 0 ? g2 : g1;
+    const long npt = g[0] * g[1] * g[2];
+    const int nblk = partv == 0 ? K1 * d : K1;
+    const size_t off = partv == 0 ? 0 : (size_t)K1 * Mv;
+    const double* src = r + off;
+    for (int dir = 0; dir < d && e == cudaSuccess; ++dir) {
+      double* dst = ((dir & 1) ? w2 : w1) + off;
+      const double* sc = (dir == d - 1) ? bs : nullptr;
+      const int cpn = partv == 0 ? d : 1;
+      const long total = npt * nblk;
+      unsigned grid = (unsigned)((total + BT - 1) / BT);
+      if (grid > 152 * 16) grid = 152 * 16;
+      if (partv == 0)
+        mass_pass<double, 2><<<grid, BT, 0, stream>>>(src, dst, g[0], g[1], g[2], dir, hh[dir], nblk, sc, cpn, M[0],
+                                                       M[1], M[2], M[4], M[5], M[8]);
+      else
+        mass_pass<double, 1><<<grid, BT, 0, stream>>>(src, dst, g[0], g[1], g[2], dir, hh[dir], nblk, sc, cpn,
+                                                       1.0 / 3.0, 1.0 / 6.0, 0.0, 0.0, 0.0, 0.0);
+      e = cudaGetLastError();
+      src = dst;
+    }
+    Mr = (d == 3) ? w1 : w2;
+  }
+  if (e == cudaSuccess) {
+    partial_dot<<<NPART, BT, 0, stream>>>(r, Mr, Nst, part);
+    finish_sum<<<1, BT, 0, stream>>>(part, NPART, 1, res);
+    e = cudaGetLastError();
+  }
+  double v = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, res, sizeof(double), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "st_mnorm_noalloc: %s\n", cudaGetErrorString(e));
+    return ST_ECUDA;
+  }
+  *out = std::sqrt(v > 0.0 ? v : 0.0);
+  return ST_OK;
+}
