@@ -16,6 +16,7 @@ ranks' DoFs over the max-over-ranks time.
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -63,6 +64,33 @@ def bytes_per_apply(p):
     ncells = p["nx"] * p["ny"] * (p["nz"] if p["dim"] == 3 else 1)
     nq, nf = (27, 11) if p["dim"] == 3 else (9, 7)
     return 8 * (3 * s["Nst"] + ncells * K1 * nq * nf)
+
+
+PROFILE = os.path.join(ROOT, "profiles", "st_jacobian_apply_fp64_3d_32cube_k1.md")
+KERNEL_SOURCES = ["st_internal.h", "st_operator.cuh", "st_face.cuh", "st_op_inst.cuh", "st_op3d.cu"]
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_28706_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of one apply from the committed ncu summary,
+    or None when the kernel sources changed since those counters were taken."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", text)
+    mt = re.search(r"traffic_bytes_per_apply:\s*([0-9]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_sources_hash():
+        return None
+    return int(mt.group(1))
 
 
 class ClockSampler:
@@ -238,15 +266,9 @@ def main():
     fl = flops_per_apply(p)
     peak = 152 * 2 * 2 * 2.070e9 / 1e12  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz
     achieved = fl / (apply_ms * 1e-3) / 1e12
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        try:
-            traffic = json.load(open(tf)).get("st_op_kernel_jac_fp64_per_apply")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "st_op_kernel<3,2,double,OP_JAC,1> (8 colour launches) + st_face_kernel + st_face_gather per apply",
+                "traffic": traffic, "kernel": "one modN apply: st_op_kernel<3,2,double,OP_JAC,1> (all cells, colour-private outputs) + st_face_kernel (side stream) + st_node_sum", "traffic_source": os.path.relpath(PROFILE, ROOT),
                 "apply_ms": apply_ms, "flops_per_apply": fl, "algorithmic_bytes_per_apply": bytes_per_apply(p),
                 "hbm_frac_of_measured": bytes_per_apply(p) / (apply_ms * 1e-3) / 6771.1e9}
 
@@ -277,15 +299,14 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        sample = int(os.environ.get("ST_ORACLE_SAMPLE_CELLS", "2048"))
+        sample = int(os.environ.get("ST_ORACLE_SAMPLE_CELLS", "32768"))
         rate, dt, cores = cpu_oracle_rate(p, U, dU, sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d random cells of the 32^3 mesh (element matrices formed and applied), Pic+exN+modN, "
-                         "%.1f s" % (sample, dt)}
-    # per apply: 8 colour launches of the volume kernel + 1 face kernel + 1 face gather;
-    # per linearisation: 8 volume + 1 face + 2 precision casts
-    ncol = 8
-    launches_per_step = len(tangents) * ((ncol + 1 + 2) + APPLIES * (ncol + 2))
+               "sample": "%d of the 32768 cells of the 32^3 mesh (element matrices formed and applied), one apply each "
+                         "of Pic, exN, modN, %.1f s" % (sample, dt)}
+    # per apply: volume kernel + face kernel + node sum; per linearisation:
+    # volume + face + 2 precision casts
+    launches_per_step = len(tangents) * ((1 + 1 + 2) + APPLIES * 3)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

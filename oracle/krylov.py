@@ -117,7 +117,16 @@ def newton(p, var, U0, vprev, f=None, vcycle_levels=1, max_iter=30, tol_abs=1e-1
                     e_new = max(e_new, safeguard)
                 eta = min(ew_max, e_new)
             forcing = eta
-        dU, its, lres = fgmres(lambda x: J @ x, R, H.vcycle, M, forcing, restart, maxit)
+        # refresh rule, second trigger, applied during the solve: with kept
+        # surrogate patches a solve that needs more than twice the preceding
+        # solve's iterations has deteriorated; the patches are rebuilt at the
+        # current iterate and the solve restarts (reading of Sec. 6.3)
+        cap = maxit if (rebuild or not lin_its) else min(maxit, 2 * lin_its[-1])
+        dU, its, lres = fgmres(lambda x: J @ x, R, H.vcycle, M, forcing, restart, cap)
+        if lres > forcing * rn * (1 + 1e-12) and cap < maxit:
+            H.update(var, U, rebuild_finest=True)
+            rebuilds += 1
+            dU, its, lres = fgmres(lambda x: J @ x, R, H.vcycle, M, forcing, restart, maxit)
         lin_its.append(its)
         if lres > forcing * rn * (1 + 1e-12):  # the linear solve missed its tolerance (Sec. 6.2)
             return U, dict(status="linear_failed", iters=m, hist=hist, lin_its=lin_its, rebuilds=rebuilds)

@@ -191,8 +191,12 @@ cudaError_t build_gather(const st_problem* h, Level& L, const std::vector<int>& 
       ptr.push_back((int)ent.size());
     }
   L.n_gather = (int)node.size();
-  if (node.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&L.d_gnode, node.size() * sizeof(int));
+  std::vector<int> gmap(L.Nq2 + L.Nq1, -1);  // node -> gather row (velocity nodes, then pressure nodes)
+  for (int t = 0; t < L.n_gather; ++t) gmap[(t < L.n_gather_vel ? 0 : L.Nq2) + node[t]] = t;
+  cudaError_t e = cudaMalloc(&L.d_gmap, gmap.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(L.d_gmap, gmap.data(), gmap.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess || node.empty()) return e;
+  e = cudaMalloc(&L.d_gnode, node.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(L.d_gnode, node.data(), node.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&L.d_gptr, ptr.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(L.d_gptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -380,6 +384,15 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
   if (e == cudaSuccess) e = cudaMalloc(&h->d_work, 3 * (size_t)F.Nst * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_Ulin, (size_t)F.Nst * sizeof(double));
   {
+    // colour-private volume outputs; zero once: each class always writes the
+    // same entries, the others stay zero
+    const size_t nb = (size_t)(1 << h->dim) * F.Nst;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cbuf64, nb * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cbuf32, nb * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_cbuf64, 0, nb * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_cbuf32, 0, nb * sizeof(float), h->stream);
+  }
+  {
     const int nout = h->dim == 3 ? 2 * 3 * 9 + 4 : 2 * 2 * 3 + 2;
     const size_t nf = (size_t)(F.nfaces > 0 ? F.nfaces : 1) * h->K1 * nout;
     if (e == cudaSuccess) e = cudaMalloc(&h->d_fscr, nf * sizeof(double));
@@ -407,7 +420,10 @@ st_status st_destroy(st_problem* h) {
     cudaFree(L.d_gnode);
     cudaFree(L.d_gptr);
     cudaFree(L.d_gent);
+    cudaFree(L.d_gmap);
   }
+  cudaFree(h->d_cbuf64);
+  cudaFree(h->d_cbuf32);
   cudaFree(h->d_cache64);
   cudaFree(h->d_fcache64);
   cudaFree(h->d_cache32);
@@ -439,9 +455,6 @@ st_status st_residual(st_problem* h, st_prec prec, const void* U, const void* v_
   if (!U || !R || !v_prev) return set_error(h, ST_EINVAL, "st_residual: U, v_prev and R are required");
   if (prec != ST_FP64 && prec != ST_FP32) return set_error(h, ST_EINVAL, "st_residual: bad precision");
   const int L = (int)h->lev.size() - 1;
-  const size_t es = prec == ST_FP64 ? 8 : 4;
-  st_status s = cuda_check(h, cudaMemsetAsync(R, 0, h->lev[L].Nst * es, h->stream), "st_residual memset");
-  if (s != ST_OK) return s;
   return cuda_check(h, launch_op(h, L, OP_RES, prec, 0, U, R, v_prev, f), "st_residual");
 }
 
@@ -478,9 +491,6 @@ st_status st_jacobian_apply(st_problem* h, st_tangent tangent, st_prec prec, con
     return set_error(h, ST_EINVAL, "st_jacobian_apply: no linearisation for this tangent (call st_linearize)");
   }
   const int L = (int)h->lev.size() - 1;
-  const size_t es = prec == ST_FP64 ? 8 : 4;
-  st_status s = cuda_check(h, cudaMemsetAsync(out, 0, h->lev[L].Nst * es, h->stream), "st_jacobian_apply memset");
-  if (s != ST_OK) return s;
   return cuda_check(h, launch_op(h, L, OP_JAC, prec, tangent, dU, out, nullptr, nullptr), "st_jacobian_apply");
 }
 

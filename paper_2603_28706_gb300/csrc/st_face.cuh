@@ -13,8 +13,8 @@
 // values/normal derivatives at the 3x3 face points (tangential passes) ->
 // tangential derivatives -> pointwise face terms -> transposed passes ->
 // compact per-slot output (values and normal-derivative weights at the face
-// nodes, pressure tests) in a scratch array.  st_face_gather then adds these
-// into the output per global node, after the volume kernels.
+// nodes, pressure tests) in a scratch array.  st_node_sum then adds these
+// into the output per global node, after the volume kernel.
 #pragma once
 
 #include "st_operator.cuh"
@@ -443,46 +443,76 @@ struct GatherEnt {
   double ed;  // weight of the face normal-derivative output
 };
 
+// Colour classes (bit mask over the two cell parities) of the cells that
+// reach node m of a 1D Q2 grid (2n+1 nodes) or Q1 grid (n+1 nodes).
+__device__ __forceinline__ int parity_mask_q2(int m, int n) {
+  if (m & 1) return 1 << (((m - 1) >> 1) & 1);
+  const int e = m >> 1;
+  return (e > 0 ? 1 << ((e - 1) & 1) : 0) | (e < n ? 1 << (e & 1) : 0);
+}
+__device__ __forceinline__ int parity_mask_q1(int m, int n) {
+  return (m > 0 ? 1 << ((m - 1) & 1) : 0) | (m < n ? 1 << (m & 1) : 0);
+}
+
+// out = sum over the colour classes reaching each slab entry of the
+// class-private volume outputs (fixed class order) + the boundary-face
+// contributions of the face scratch (CSR row of the node, if any).
+// One thread per slab entry; writes every entry of out.
 template <int DIM, int K1, typename T>
-__global__ void st_face_gather(const OpArgs a, int nvel, const int* __restrict__ gnode, const int* __restrict__ gptr,
-                               const GatherEnt* __restrict__ gent, int ntot, const T* __restrict__ fscr,
-                               T* __restrict__ out) {
+__global__ void st_node_sum(const OpArgs a, const int* __restrict__ gmap, const int* __restrict__ gptr,
+                            const GatherEnt* __restrict__ gent, const T* __restrict__ fscr, T* __restrict__ out) {
   using D = Dims<DIM>;
-  constexpr int NC = D::NC, NFQ = D::NFQ, NFP = D::NFP;
-  constexpr int NOUT = 2 * NC * NFQ + NFP;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntot; t += gridDim.x * blockDim.x) {
-    const int node = gnode[t];
-    const int b = gptr[t], e = gptr[t + 1];
-    if (t < nvel) {
-      T acc[K1 * NC];
+  constexpr int NC = D::NC, NFQ = D::NFQ;
+  constexpr int NOUT = 2 * NC * NFQ + D::NFP;
+  const T* cb = reinterpret_cast<const T*>(a.cbuf);
+  const long nvel = (long)K1 * a.Mv, ntot = nvel + (long)K1 * a.Mp;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < ntot; idx += (long)gridDim.x * blockDim.x) {
+    int mx, my, mz = 1, row, mu, comp = 0;
+    if (idx < nvel) {
+      mu = (int)(idx / a.Mv);
+      const long r = idx - (long)mu * a.Mv;
+      comp = (int)(r / a.Nq2);
+      const long g = r - (long)comp * a.Nq2;
+      const int gx = (int)(g % a.g2[0]), gy = (int)((g / a.g2[0]) % a.g2[1]);
+      mx = parity_mask_q2(gx, a.n[0]);
+      my = parity_mask_q2(gy, a.n[1]);
+      if (DIM == 3) mz = parity_mask_q2((int)(g / (a.g2[0] * a.g2[1])), a.n[2]);
+      row = gmap[g];
+    } else {
+      const long r = idx - nvel;
+      mu = (int)(r / a.Mp);
+      const long g = r - (long)mu * a.Mp;
+      const int gx = (int)(g % a.g1[0]), gy = (int)((g / a.g1[0]) % a.g1[1]);
+      mx = parity_mask_q1(gx, a.n[0]);
+      my = parity_mask_q1(gy, a.n[1]);
+      if (DIM == 3) mz = parity_mask_q1((int)(g / (a.g1[0] * a.g1[1])), a.n[2]);
+      row = gmap[a.Nq2 + g];
+    }
+    T acc = 0;
 #pragma unroll
-      for (int i = 0; i < K1 * NC; ++i) acc[i] = 0;
-      for (int j = b; j < e; ++j) {
-        const GatherEnt g = gent[j];
-        const T ev = (T)g.e, ed = (T)g.ed;
+    for (int pz = 0; pz < 2; ++pz)
 #pragma unroll
-        for (int mu = 0; mu < K1; ++mu) {
-          const T* fs = fscr + ((long)g.fid * K1 + mu) * NOUT + g.tn;
+      for (int py = 0; py < 2; ++py)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) acc[mu * NC + c] += ev * fs[c * NFQ] + ed * fs[NC * NFQ + c * NFQ];
+        for (int px = 0; px < 2; ++px)
+          if (((mz >> pz) & 1) && ((my >> py) & 1) && ((mx >> px) & 1))
+            acc += cb[(long)(px | (py << 1) | (pz << 2)) * a.cbuf_stride + idx];
+    if (row >= 0) {
+      const int b = gptr[row], e = gptr[row + 1];
+      if (idx < nvel) {
+        for (int j = b; j < e; ++j) {
+          const GatherEnt ge = gent[j];
+          const T* fs = fscr + ((long)ge.fid * K1 + mu) * NOUT + ge.tn + comp * NFQ;
+          acc += (T)ge.e * fs[0] + (T)ge.ed * fs[NC * NFQ];
+        }
+      } else {
+        for (int j = b; j < e; ++j) {
+          const GatherEnt ge = gent[j];
+          acc += fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
         }
       }
-#pragma unroll
-      for (int mu = 0; mu < K1; ++mu)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) out[(long)mu * a.Mv + (long)c * a.Nq2 + node] += acc[mu * NC + c];
-    } else {
-      T acc[K1];
-#pragma unroll
-      for (int i = 0; i < K1; ++i) acc[i] = 0;
-      for (int j = b; j < e; ++j) {
-        const GatherEnt g = gent[j];
-#pragma unroll
-        for (int mu = 0; mu < K1; ++mu) acc[mu] += fscr[((long)g.fid * K1 + mu) * NOUT + 2 * NC * NFQ + g.tn];
-      }
-#pragma unroll
-      for (int mu = 0; mu < K1; ++mu) out[(long)K1 * a.Mv + (long)mu * a.Mp + node] += acc[mu];
     }
+    out[idx] = acc;
   }
 }
 

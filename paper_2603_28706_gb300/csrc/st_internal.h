@@ -52,10 +52,11 @@ struct OpArgs {
   double KtV[MAX_K1 * MAX_K1];  // K_t * cell volume
   double Kt[MAX_K1 * MAX_K1];
   double mt[MAX_K1];
-  // colour class
-  int colour;
-  int cn[3], c0[3];
+  // range of colour-ordered cells (or element-matrix items) of the launch
   long col_start, ncol;
+  // colour-private output buffers: class c writes cbuf + c * cbuf_stride
+  void* cbuf;
+  long cbuf_stride;
   // physics
   double p, delta, nu, nu_inf, sigma_max, gamma1, gamma2, q_sign, vbar;
   double L[3];
@@ -73,7 +74,8 @@ struct OpArgs {
   double* wfcache;
   const int* face_off;     // first boundary face of every cell (linear order)
   int* err;                // device error flag
-  // element-matrix mode: all colour classes, fixed node mu, output matrices
+  // colour classes (first colour-ordered index, extents); element-matrix
+  // mode: fixed node mu, output matrices
   long col_start_all[9];
   int cn_all[8][3];
   int elm_mu;              // coefficient-cache node of the matrices
@@ -113,6 +115,7 @@ struct Level {
   int* d_gnode = nullptr;
   int* d_gptr = nullptr;
   void* d_gent = nullptr;
+  int* d_gmap = nullptr;       // Nq2 + Nq1: gather row of every velocity / pressure node, -1 off the boundary layer
   // Vanka / coarse operator storage (set up by the preconditioner)
 };
 
@@ -139,6 +142,8 @@ struct st_problem {
   double* d_work = nullptr;        // 3 finest-level slab vectors (mass operator work)
   double* d_Ulin = nullptr;        // copy of the state of the last linearisation
   double* d_fscr = nullptr;         // compact per-face-slot outputs of the face kernel (FP64 or FP32 view)
+  void* d_cbuf64 = nullptr;        // 2^dim colour-private FP64 slab vectors of the volume kernel
+  void* d_cbuf32 = nullptr;        // the same in FP32 (entries no cell of a class touches stay zero)
   cudaStream_t s_face = nullptr;   // internal stream: face kernels overlap the volume kernels
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string last_error;

@@ -642,9 +642,9 @@ cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
   // y = A_l x
   const Level& L = h->lev[l];
   const int prec = sizeof(T) == 8 ? ST_FP64 : ST_FP32;
+  if (l == (int)h->lev.size() - 1) return launch_op(h, l, OP_JAC, prec, h->lin_tangent, x, y, nullptr, nullptr);
   cudaError_t e = cudaMemsetAsync(y, 0, L.Nst * sizeof(T), h->stream);
   if (e != cudaSuccess) return e;
-  if (l == (int)h->lev.size() - 1) return launch_op(h, l, OP_JAC, prec, h->lin_tangent, x, y, nullptr, nullptr);
   PatchArgs pa = patch_args(h, l, false);
   for (int c = 0; c < (1 << h->dim); ++c) {
     const long ncol = L.col_start[c + 1] - L.col_start[c];

@@ -25,11 +25,12 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
     if (focc < 1) focc = 1;
   }
   // The face kernel (all boundary faces, one launch) runs on an internal
-  // stream concurrently with the volume kernels; it writes only the face
-  // scratch (or, when linearising, the face cache).  The volume kernels run
-  // colour by colour on the caller's stream and scatter-add into `out`.  The
-  // caller's stream then waits for the face kernel and st_face_gather adds the
-  // face contributions into `out`, one thread per node.
+  // stream concurrently with the volume kernel; it writes only the face
+  // scratch (or, when linearising, the face cache).  The volume kernel (one
+  // launch over all cells in colour order) writes every cell's contributions
+  // into the private buffer of its colour class with plain stores.  The
+  // caller's stream then waits for the face kernel and st_node_sum forms
+  // out = sum of the class buffers + face contributions, one thread per entry.
   cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
   if (e != cudaSuccess) return e;
@@ -44,22 +45,16 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int ncolours = 1 << DIM;
-  for (int c = 0; c < ncolours; ++c) {
-    const long ncol = L.col_start[c + 1] - L.col_start[c];
-    if (ncol == 0) continue;
-    a.colour = c;
-    for (int d = 0; d < 3; ++d) {
-      a.cn[d] = L.cn[c][d];
-      a.c0[d] = L.c0[c][d];
-    }
-    a.col_start = L.col_start[c];
-    a.ncol = ncol;
-    // every resident CTA slot gets an equal share of the colour class when there
-    // is at least half a batch per slot; smaller classes use full batches
+  a.col_start = 0;
+  a.ncol = L.ncells;
+  a.cbuf = sizeof(T) == 8 ? h->d_cbuf64 : h->d_cbuf32;
+  a.cbuf_stride = L.Nst;
+  {
+    // every resident CTA slot gets an equal share of the cells when there are
+    // at least half a batch per slot; smaller meshes use full batches
     const long cap = (long)occ * h->nsm;
-    long grid = (ncol + Cfg::C - 1) / Cfg::C;
-    if (ncol >= cap * (Cfg::C / 2)) grid = cap;
+    long grid = (L.ncells + Cfg::C - 1) / Cfg::C;
+    if (L.ncells >= cap * (Cfg::C / 2)) grid = cap;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
@@ -69,12 +64,12 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   e = cudaEventRecord(h->ev_join, h->s_face);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   if (e != cudaSuccess) return e;
-  if (MODE != OP_LIN && nslots > 0 && L.n_gather > 0) {
-    long g = (L.n_gather + 255) / 256;
+  if (MODE != OP_LIN) {
+    long g = (L.Nst + 255) / 256;
     if (g > 16L * h->nsm) g = 16L * h->nsm;
-    st_face_gather<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(
-        a, L.n_gather_vel, L.d_gnode, L.d_gptr, reinterpret_cast<const GatherEnt*>(L.d_gent), L.n_gather, fscr,
-        reinterpret_cast<T*>(a.out));
+    st_node_sum<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(a, L.d_gmap, L.d_gptr,
+                                                                reinterpret_cast<const GatherEnt*>(L.d_gent), fscr,
+                                                                reinterpret_cast<T*>(a.out));
     e = cudaGetLastError();
   }
   return e;

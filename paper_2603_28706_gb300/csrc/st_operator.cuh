@@ -208,6 +208,11 @@ __device__ __forceinline__ void rpass_acc(T* acc, const MT* m, const T* g) {
 
 // colour-ordered index of a linear cell id (the coefficient caches use it)
 template <int DIM>
+__device__ __forceinline__ int colour_of(int ex, int ey, int ez) {
+  return (ex & 1) | ((ey & 1) << 1) | (DIM == 3 ? ((ez & 1) << 2) : 0);
+}
+
+template <int DIM>
 __device__ __forceinline__ long colour_index(const OpArgs& a, int cell) {
   const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
   const int c = (ex & 1) | ((ey & 1) << 1) | ((ez & 1) << 2);
@@ -217,8 +222,8 @@ __device__ __forceinline__ long colour_index(const OpArgs& a, int cell) {
 template <int DIM, int K1, typename T>
 struct OpCfg {
   using D = Dims<DIM>;
-  static constexpr int NT = DIM == 3 ? 96 : 128;       // threads per CTA
-  static constexpr int SLOTS = DIM == 3 ? 32 : 64;     // target (cell, node) slots per batch
+  static constexpr int NT = DIM == 3 ? 128 : 128;  // threads per CTA (2 CTAs per SM: 2 warps per scheduler)
+  static constexpr int SLOTS = DIM == 3 ? 36 : 64;  // target (cell, node) slots per batch
   static constexpr int C = SLOTS / K1 > 0 ? SLOTS / K1 : 1;
   static constexpr int S = C * K1;
   // per-slot shared arrays (elements of T): qp values, gradients/fluxes, nodal pressure, pressure-test flux
@@ -246,9 +251,8 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
   int* sCell = reinterpret_cast<int*>(sQ + S * Cfg::SQ);  // linear cell id of batch cell
 
   const T* in = reinterpret_cast<const T*>(a.in);
-  T* out = reinterpret_cast<T*>(a.out);
 
-  // balanced chunk of the colour class
+  // balanced chunk of the colour-ordered cells (element-matrix mode: of the items)
   const long ncol = a.ncol;
   const long cbeg = (long)blockIdx.x * ncol / gridDim.x;
   const long cend = (long)(blockIdx.x + 1) * ncol / gridDim.x;
@@ -274,11 +278,17 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
       if constexpr (MODE == OP_ELM) {
         sCell[ci] = (int)((b0 + ci) / D::NE);
       } else {
-        const long li = b0 + ci;  // index within the colour class
-        const int i = (int)(li % a.cn[0]);
-        const int j = (int)((li / a.cn[0]) % a.cn[1]);
-        const int l = (int)(li / ((long)a.cn[0] * a.cn[1]));
-        const int ex = a.c0[0] + 2 * i, ey = a.c0[1] + 2 * j, ez = (DIM == 3) ? a.c0[2] + 2 * l : 0;
+        // colour-ordered cell index -> colour class c -> cell (o + 2 i, ...)
+        long li = b0 + ci;
+        int c = 0;
+#pragma unroll
+        for (int cc = 1; cc < (1 << DIM); ++cc) c += (li >= a.col_start_all[cc]) ? 1 : 0;
+        li -= a.col_start_all[c];
+        const int cn0 = a.cn_all[c][0], cn1 = a.cn_all[c][1];
+        const int i = (int)(li % cn0);
+        const int j = (int)((li / cn0) % cn1);
+        const int l = (int)(li / ((long)cn0 * cn1));
+        const int ex = (c & 1) + 2 * i, ey = ((c >> 1) & 1) + 2 * j, ez = (DIM == 3) ? ((c >> 2) & 1) + 2 * l : 0;
         sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
       }
     }
@@ -550,14 +560,11 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
             for (int q = 0; q < NQ; ++q) E[(long)(c * NQ + q) * D::NE] = acc[q];
             continue;
           }
-          // scatter-add (cells of one colour class share no node): all loads
-          // first so that they are in flight together, then the stores
-          T* ob = out + (long)mu * a.Mv + c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) {
-            const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-            acc[q] += ob[qx + a.g2[0] * (qy + a.g2[1] * qz)];
-          }
+          // plain stores into the private buffer of the cell's colour class:
+          // cells of one class share no node, so no two threads write the same
+          // entry; st_node_sum adds the classes' buffers afterwards
+          T* ob = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)mu * a.Mv +
+                  c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
@@ -580,7 +587,8 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
           }
           const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
           const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
-          out[(long)K1 * a.Mv + (long)mu * a.Mp + g] += acc;
+          reinterpret_cast<T*>(a.cbuf)[(long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
+                                       (long)mu * a.Mp + g] = acc;
         }
       }
     }

@@ -7,7 +7,9 @@
 // preconditioner is one V-cycle in FP32 (mixed) or FP64.
 // Newton: R = R_n(U); stop by eq. nk-stop; linearise; rebuild the finest-level
 // surrogate patches only by the refresh rule of Sec. 6.3 (coarse operators and
-// the matrix-free operator always follow the iterate); solve J dU = R to the
+// the matrix-free operator always follow the iterate; a solve with kept
+// patches that passes twice the preceding solve's iteration count is stopped,
+// the patches are rebuilt and the solve restarts); solve J dU = R to the
 // Eisenstat-Walker forcing (choice 2; Picard: lin_rtol); Armijo backtracking
 // on phi = 1/2 |R|_M^2 (exN, modN; Picard takes lambda = 1); U += lambda dU.
 #include <cmath>
@@ -103,8 +105,6 @@ cudaError_t mnorm(st_problem* h, KrylovWs* k, const double* v, double& out) {
 
 cudaError_t japply(st_problem* h, const double* x, double* y) {
   const int L = (int)h->lev.size() - 1;
-  cudaError_t e = cudaMemsetAsync(y, 0, h->lev[L].Nst * sizeof(double), h->stream);
-  if (e != cudaSuccess) return e;
   return launch_op(h, L, OP_JAC, ST_FP64, h->lin_tangent, x, y, nullptr, nullptr);
 }
 
@@ -282,8 +282,20 @@ extern "C" st_status st_newton_step(st_problem* h, st_tangent tangent, st_prec v
     }
     int its = 0;
     double lres = 0.0, bn = 0.0;
-    st = fgmres(h, k, vcycle_prec, k->R, forcing, P.fgmres_maxit, its, lres, bn);
+    // refresh rule, second trigger, applied during the solve: with kept
+    // surrogate patches a solve that needs more than twice the preceding
+    // solve's iterations has deteriorated; rebuild them and restart the solve
+    const int cap = (rebuild || lin_last < 0) ? P.fgmres_maxit : std::min(P.fgmres_maxit, 2 * lin_last);
+    st = fgmres(h, k, vcycle_prec, k->R, forcing, cap, its, lres, bn);
     if (st != ST_OK) return st;
+    if (lres > forcing * bn * (1.0 + 1e-12) && cap < P.fgmres_maxit) {
+      inf.fgmres_iters_total += its;
+      st = mg_setup(h, vcycle_prec, true);
+      if (st != ST_OK) return st;
+      inf.patch_rebuilds += 1;
+      st = fgmres(h, k, vcycle_prec, k->R, forcing, P.fgmres_maxit, its, lres, bn);
+      if (st != ST_OK) return st;
+    }
     inf.fgmres_iters_total += its;
     inf.fgmres_iters_last = its;
     lin_prev = lin_last;
