@@ -93,7 +93,7 @@ typedef struct {
   int newton_iters;           /* nonlinear iterations taken                          */
   int fgmres_iters_total;     /* FGMRES iterations over all Newton steps             */
   int fgmres_iters_last;
-  int patch_rebuilds;         /* surrogate patch factorisations built                */
+  int patch_rebuilds;         /* surrogate patch inverses built                      */
   double lambda_last;         /* last accepted damping                               */
   double res_norm_initial;    /* |R_n(U^0)|_M                                        */
   double res_norm_final;      /* |R_n(U^m)|_M at exit                                */
@@ -151,7 +151,8 @@ st_status st_mnorm(st_problem* h, const void* r, double* out);
  * linearisation: finest-level surrogate patch matrices with the coefficients
  * frozen at t_rep = midpoint of I_n (eq. surrogate-diag), Galerkin coarse
  * operators A_l = P^T A_{l+1} P (Sec. 6.3) and their exact cell patches,
- * batched LU factorisations, the coarsest-level factorisation.  prec: FP32
+ * inverted explicitly (batched Gauss-Jordan with partial pivoting), on every
+ * level including the coarsest.  prec: FP32
  * (mixed) or FP64 storage/arithmetic of the smoother.  Called implicitly by
  * st_vanka_smooth / st_vcycle when missing. */
 st_status st_precond_setup(st_problem* h, st_prec prec);

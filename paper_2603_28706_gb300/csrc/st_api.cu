@@ -39,6 +39,16 @@ void build_consts(const RefTables& R, ConstTables& t, ConstTablesF& tf) {
     t.Bt[i] = R.Bt[i];
     t.Dc[i] = R.Dc[i];
   }
+  const double* mats[2] = {R.B, R.Bt};
+  double* outs[2] = {t.BS, t.BtS};
+  for (int k = 0; k < 2; ++k) {
+    const double* m = mats[k];
+    outs[k][0] = 0.5 * (m[0] + m[2]);
+    outs[k][1] = 0.5 * (m[0] - m[2]);
+    outs[k][2] = m[1];
+    outs[k][3] = m[3];
+    outs[k][4] = m[4];
+  }
   for (int i = 0; i < 3; ++i) t.W[i] = R.W[i];
   for (int i = 0; i < 6; ++i) {
     t.B1[i] = R.B1[i];

@@ -443,21 +443,11 @@ struct GatherEnt {
   double ed;  // weight of the face normal-derivative output
 };
 
-// Colour classes (bit mask over the two cell parities) of the cells that
-// reach node m of a 1D Q2 grid (2n+1 nodes) or Q1 grid (n+1 nodes).
-__device__ __forceinline__ int parity_mask_q2(int m, int n) {
-  if (m & 1) return 1 << (((m - 1) >> 1) & 1);
-  const int e = m >> 1;
-  return (e > 0 ? 1 << ((e - 1) & 1) : 0) | (e < n ? 1 << (e & 1) : 0);
-}
-__device__ __forceinline__ int parity_mask_q1(int m, int n) {
-  return (m > 0 ? 1 << ((m - 1) & 1) : 0) | (m < n ? 1 << (m & 1) : 0);
-}
-
-// out = sum over the colour classes reaching each slab entry of the
-// class-private volume outputs (fixed class order) + the boundary-face
-// contributions of the face scratch (CSR row of the node, if any).
-// One thread per slab entry; writes every entry of out.
+// out = sum of the 2^DIM class-private volume outputs (entries a class does
+// not reach are zero in its buffer, so every class is added, in a fixed
+// order: coalesced, branch-free) + the boundary-face contributions of the
+// face scratch (CSR row of the node, if any).  One thread per slab entry;
+// writes every entry of out.
 template <int DIM, int K1, typename T>
 __global__ void st_node_sum(const OpArgs a, const int* __restrict__ gmap, const int* __restrict__ gptr,
                             const GatherEnt* __restrict__ gent, const T* __restrict__ fscr, T* __restrict__ out) {
@@ -467,36 +457,23 @@ __global__ void st_node_sum(const OpArgs a, const int* __restrict__ gmap, const 
   const T* cb = reinterpret_cast<const T*>(a.cbuf);
   const long nvel = (long)K1 * a.Mv, ntot = nvel + (long)K1 * a.Mp;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < ntot; idx += (long)gridDim.x * blockDim.x) {
-    int mx, my, mz = 1, row, mu, comp = 0;
+    T v[1 << DIM];
+#pragma unroll
+    for (int c = 0; c < (1 << DIM); ++c) v[c] = cb[(long)c * a.cbuf_stride + idx];
+    T acc = v[0];
+#pragma unroll
+    for (int c = 1; c < (1 << DIM); ++c) acc += v[c];
+    int row, mu, comp = 0;
     if (idx < nvel) {
       mu = (int)(idx / a.Mv);
       const long r = idx - (long)mu * a.Mv;
       comp = (int)(r / a.Nq2);
-      const long g = r - (long)comp * a.Nq2;
-      const int gx = (int)(g % a.g2[0]), gy = (int)((g / a.g2[0]) % a.g2[1]);
-      mx = parity_mask_q2(gx, a.n[0]);
-      my = parity_mask_q2(gy, a.n[1]);
-      if (DIM == 3) mz = parity_mask_q2((int)(g / (a.g2[0] * a.g2[1])), a.n[2]);
-      row = gmap[g];
+      row = gmap[r - (long)comp * a.Nq2];
     } else {
       const long r = idx - nvel;
       mu = (int)(r / a.Mp);
-      const long g = r - (long)mu * a.Mp;
-      const int gx = (int)(g % a.g1[0]), gy = (int)((g / a.g1[0]) % a.g1[1]);
-      mx = parity_mask_q1(gx, a.n[0]);
-      my = parity_mask_q1(gy, a.n[1]);
-      if (DIM == 3) mz = parity_mask_q1((int)(g / (a.g1[0] * a.g1[1])), a.n[2]);
-      row = gmap[a.Nq2 + g];
+      row = gmap[a.Nq2 + (r - (long)mu * a.Mp)];
     }
-    T acc = 0;
-#pragma unroll
-    for (int pz = 0; pz < 2; ++pz)
-#pragma unroll
-      for (int py = 0; py < 2; ++py)
-#pragma unroll
-        for (int px = 0; px < 2; ++px)
-          if (((mz >> pz) & 1) && ((my >> py) & 1) && ((mx >> px) & 1))
-            acc += cb[(long)(px | (py << 1) | (pz << 2)) * a.cbuf_stride + idx];
     if (row >= 0) {
       const int b = gptr[row], e = gptr[row + 1];
       if (idx < nvel) {

@@ -1,6 +1,6 @@
 // Space-time multigrid preconditioner (Sec. 6.3): nested Q2/Q1 transfers,
-// Galerkin coarse operators, exact and surrogate cell patches, batched LU,
-// additive Vanka sweeps and the V-cycle.
+// Galerkin coarse operators, exact and surrogate cell patches, batched
+// Gauss-Jordan patch inverses, additive Vanka sweeps and the V-cycle.
 //
 // Data per level l (0 = coarsest, L = finest):
 //   E_l   spatial element matrices (times tau w_mu) of every cell and node mu,
@@ -9,7 +9,7 @@
 //         sum-factorised operator, faces directly), on l < L by Galerkin
 //         coarsening E_l = sum_children P_c^T E_{l+1} P_c (exact for nested
 //         spaces, identity in time, so A_l = P^T A_{l+1} P);
-//   LU_l  LU factors (partial pivoting, column-major) of the cell patches
+//   LU_l  explicit inverses (Gauss-Jordan, partial pivoting, column-major) of the cell patches
 //         A_{l,K} = R_K A_l R_K^T (l < L) resp. the surrogate A~_{L,K}
 //         (eq. surrogate-diag: every node's spatial block replaced by the one
 //         at t_rep = slab midpoint, temporal matrices unchanged).
@@ -263,18 +263,25 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
   }
 }
 
-// ------------------------------------------------------------ batched LU
-// In-place LU with partial pivoting of `count` matrices of size N stored
-// column-major (F[col][row]); one CTA per matrix.  A zero pivot sets err[0].
+// ------------------------------------------------------- batched inverse
+// In-place Gauss-Jordan inversion with partial (row) pivoting of `count`
+// matrices of size N stored column-major (F[col][row]); one CTA per matrix.
+// Step k: pivot row p = argmax_{i>=k} |a_ik| (lowest index on ties), swap rows
+// k and p, scale row k by 1/a_kk with the pivot entry replaced by 1, and
+// subtract multiples of it from every other row, with column k replaced by
+// zero first.  After the last step the columns are permuted back in reverse
+// pivot order, which leaves A^{-1}.  A zero pivot sets err[0].
 template <typename T>
-__global__ void lu_kernel(T* __restrict__ F, int* __restrict__ piv, int N, long count, int* __restrict__ err) {
+__global__ void gj_invert_kernel(T* __restrict__ F, int* __restrict__ piv, int N, long count,
+                                 int* __restrict__ err) {
   __shared__ int s_piv;
   __shared__ T s_val[256];
   __shared__ int s_idx[256];
+  __shared__ T s_row[MAXN], s_col[MAXN];
   for (long m = blockIdx.x; m < count; m += gridDim.x) {
     T* A = F + m * (long)N * N;
+    int* pv = piv + m * N;
     for (int k = 0; k < N; ++k) {
-      // pivot search in column k, rows k..N-1
       T best = -1;
       int bi = k;
       for (int i = k + threadIdx.x; i < N; i += blockDim.x) {
@@ -300,39 +307,51 @@ __global__ void lu_kernel(T* __restrict__ F, int* __restrict__ piv, int N, long 
       }
       if (threadIdx.x == 0) {
         s_piv = s_idx[0];
-        piv[m * N + k] = s_piv;
+        pv[k] = s_piv;
         if (!(s_val[0] > 0)) atomicExch(err, 1);
       }
       __syncthreads();
       const int p = s_piv;
-      if (p != k)
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-          const T t = A[(long)j * N + k];
-          A[(long)j * N + k] = A[(long)j * N + p];
-          A[(long)j * N + p] = t;
-        }
-      __syncthreads();
-      const T d = A[(long)k * N + k];
+      const T d = A[(long)k * N + p];
       const T inv = d != (T)0 ? (T)1 / d : (T)0;
-      for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) A[(long)k * N + i] *= inv;
-      __syncthreads();
-      const int rem = N - k - 1;
-      for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
-        const int jj = k + 1 + t / rem, ii = k + 1 + t % rem;
-        A[(long)jj * N + ii] -= A[(long)k * N + ii] * A[(long)jj * N + k];
+      // pivot row (swapped into k) scaled, pivot entry -> 1/d; multipliers of column k
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const T rk = A[(long)j * N + p];
+        if (p != k) A[(long)j * N + p] = A[(long)j * N + k];
+        s_row[j] = (j == k ? (T)1 : rk) * inv;
       }
+      __syncthreads();
+      for (int i = threadIdx.x; i < N; i += blockDim.x) s_col[i] = (i == k) ? (T)0 : A[(long)k * N + i];
+      __syncthreads();
+      for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) {
+        const int j = (int)(t / N), i = (int)(t % N);
+        T* aij = A + t;
+        if (i == k) *aij = s_row[j];
+        else *aij = (j == k ? (T)0 : *aij) - s_col[i] * s_row[j];
+      }
+      __syncthreads();
+    }
+    for (int k = N - 1; k >= 0; --k) {
+      const int p = pv[k];
+      if (p != k)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+          const T t = A[(long)k * N + i];
+          A[(long)k * N + i] = A[(long)p * N + i];
+          A[(long)p * N + i] = t;
+        }
       __syncthreads();
     }
   }
 }
 
 // ------------------------------------------------------------ Vanka solve
-// For the patches (cells) of one colour class: x = A_K^{-1} defect|_K by the LU
-// factors, then d|_K += omega x (cells of one class share no dof).
+// For the patches (cells) of one colour class: x = A_K^{-1} defect|_K with the
+// explicit inverse (a matrix-vector product streamed column by column), then
+// d|_K += omega x (cells of one class share no dof).
 template <int DIM, typename T>
-__global__ void vanka_patch_solve(const T* __restrict__ F, const int* __restrict__ piv, int K1, const T* __restrict__ defect,
-                                  T* __restrict__ d, int n0, int n1, int n2, int c0x, int c0y, int c0z, int cnx, int cny,
-                                  long ncol, double omega, long Nq2, long Nq1, long Mv, long Mp) {
+__global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __restrict__ defect, T* __restrict__ d,
+                                  int n0, int n1, int n2, int c0x, int c0y, int c0z, int cnx, int cny, long ncol,
+                                  double omega, long Nq2, long Nq1, long Mv, long Mp) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE;
   __shared__ T sx[MAXN];
@@ -357,32 +376,12 @@ __global__ void vanka_patch_solve(const T* __restrict__ F, const int* __restrict
       sx[r] = defect[g];
     }
     __syncthreads();
-    // row interchanges, in factorisation order
-    if (threadIdx.x == 0)
-      for (int k = 0; k < N; ++k) {
-        const int p = piv[cell * N + k];
-        if (p != k) {
-          const T t = sx[k];
-          sx[k] = sx[p];
-          sx[p] = t;
-        }
-      }
-    __syncthreads();
-    // forward substitution (unit lower), column oriented
-    for (int k = 0; k < N - 1; ++k) {
-      const T xk = sx[k];
-      for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) sx[i] -= A[(long)k * N + i] * xk;
-      __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      T acc = 0;
+#pragma unroll 8
+      for (int j = 0; j < N; ++j) acc = fma(A[(long)j * N + r], sx[j], acc);
+      d[sg[r]] += (T)omega * acc;
     }
-    // backward substitution
-    for (int k = N - 1; k >= 0; --k) {
-      if (threadIdx.x == 0) sx[k] /= A[(long)k * N + k];
-      __syncthreads();
-      const T xk = sx[k];
-      for (int i = threadIdx.x; i < k; i += blockDim.x) sx[i] -= A[(long)k * N + i] * xk;
-      __syncthreads();
-    }
-    for (int r = threadIdx.x; r < N; r += blockDim.x) d[sg[r]] += (T)omega * sx[r];
     __syncthreads();
   }
 }
@@ -679,11 +678,11 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
       const unsigned g = (unsigned)(ncol < 16L * h->nsm ? ncol : 16L * h->nsm);
       const int nt = N <= 128 ? 128 : 256;
       if (h->dim == 2)
-        vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, D.piv, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
+        vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
                                                          L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
                                                          L.cn[c][1], ncol, h->P.omega, L.Nq2, L.Nq1, L.Mv, L.Mp);
       else
-        vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, D.piv, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
+        vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
                                                          L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
                                                          L.cn[c][1], ncol, h->P.omega, L.Nq2, L.Nq1, L.Mv, L.Mp);
       e = cudaGetLastError();
@@ -880,13 +879,13 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
       else patch_assemble<3, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        lu_kernel<double><<<g, 256, 0, h->stream>>>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
+        gj_invert_kernel<double><<<g, 256, 0, h->stream>>>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
     } else {
       if (h->dim == 2) patch_assemble<2, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       else patch_assemble<3, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        lu_kernel<float><<<g, 256, 0, h->stream>>>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
+        gj_invert_kernel<float><<<g, 256, 0, h->stream>>>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
   }

@@ -39,6 +39,7 @@ namespace st {
 // mesh-independent reference tables in constant memory (double and float)
 struct ConstTables {
   double B[9], Bt[9], Dc[9], W[3], B1[6], E[6], ED[6];
+  double BS[5], BtS[5];      // even/odd form of B, Bt (see rpass_sym)
   double WQ3[27], WQ2[9];    // tensor Gauss weights on the unit cell
   double PSI3[27 * 8], PSI2[9 * 4];  // Q1 basis at the cell Gauss points
   double FW3[9], FW2[3];     // tensor Gauss weights on a unit face
@@ -46,6 +47,7 @@ struct ConstTables {
 };
 struct ConstTablesF {
   float B[9], Bt[9], Dc[9], W[3], B1[6], E[6], ED[6];
+  float BS[5], BtS[5];
   float WQ3[27], WQ2[9];
   float PSI3[27 * 8], PSI2[9 * 4];
   float FW3[9], FW2[3];
@@ -171,6 +173,59 @@ __device__ __forceinline__ void rpass(T* v, const MT* m) {
     v[b] = m0 * x0 + m1 * x1 + m2 * x2;
     v[b + st] = m3 * x0 + m4 * x1 + m5 * x2;
     v[b + 2 * st] = m6 * x0 + m7 * x1 + m8 * x2;
+  }
+}
+
+// in-place pass v <- M v along DIR for a centro-symmetric M (M[2-i][2-j] =
+// M[i][j]) given in even/odd form cs = {(m00+m02)/2, (m00-m02)/2, m01, m10,
+// m11}: with e = x0 + x2, o = x0 - x2 every line costs 8 FP operations
+// instead of 9
+template <int DIM, int DIR, typename T, typename MT>
+__device__ __forceinline__ void rpass_sym(T* v, const MT* cs) {
+  constexpr int NL = Dims<DIM>::NL, st = lstride<DIR>();
+  const T s = (T)cs[0], t = (T)cs[1], m1 = (T)cs[2], m3 = (T)cs[3], m4 = (T)cs[4];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int b = lbase<DIM, DIR>(l);
+    const T x0 = v[b], x1 = v[b + st], x2 = v[b + 2 * st];
+    const T e = x0 + x2, o = x0 - x2;
+    const T c = fma(s, e, m1 * x1);
+    v[b] = fma(t, o, c);
+    v[b + st] = fma(m3, e, m4 * x1);
+    v[b + 2 * st] = fma(-t, o, c);
+  }
+}
+
+// dst <- D v along DIR (dst in shared memory) for a centro-antisymmetric D,
+// whose centre entry is zero
+template <int DIM, int DIR, typename T, typename MT>
+__device__ __forceinline__ void rpass_out_d(const T* v, const MT* m, T* dst) {
+  constexpr int NL = Dims<DIM>::NL, st = lstride<DIR>();
+  const T m0 = (T)m[0], m1 = (T)m[1], m2 = (T)m[2], m3 = (T)m[3], m5 = (T)m[5], m6 = (T)m[6], m7 = (T)m[7],
+          m8 = (T)m[8];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int b = lbase<DIM, DIR>(l);
+    const T x0 = v[b], x1 = v[b + st], x2 = v[b + 2 * st];
+    dst[b] = fma(m2, x2, fma(m1, x1, m0 * x0));
+    dst[b + st] = fma(m5, x2, m3 * x0);
+    dst[b + 2 * st] = fma(m8, x2, fma(m7, x1, m6 * x0));
+  }
+}
+
+// acc <- acc + D g along DIR (g in shared memory), D as in rpass_out_d
+template <int DIM, int DIR, typename T, typename MT>
+__device__ __forceinline__ void rpass_acc_d(T* acc, const MT* m, const T* g) {
+  constexpr int NL = Dims<DIM>::NL, st = lstride<DIR>();
+  const T m0 = (T)m[0], m1 = (T)m[1], m2 = (T)m[2], m3 = (T)m[3], m5 = (T)m[5], m6 = (T)m[6], m7 = (T)m[7],
+          m8 = (T)m[8];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int b = lbase<DIM, DIR>(l);
+    const T x0 = g[b], x1 = g[b + st], x2 = g[b + 2 * st];
+    acc[b] = fma(m2, x2, fma(m1, x1, fma(m0, x0, acc[b])));
+    acc[b + st] = fma(m5, x2, fma(m3, x0, acc[b + st]));
+    acc[b + 2 * st] = fma(m8, x2, fma(m7, x1, fma(m6, x0, acc[b + 2 * st])));
   }
 }
 
@@ -346,15 +401,15 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
       T v[NQ];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) v[q] = xs[q];
-      rpass<DIM, 0>(v, ct.B);
-      rpass<DIM, 1>(v, ct.B);
-      if constexpr (DIM == 3) rpass<DIM, 2>(v, ct.B);
+      rpass_sym<DIM, 0>(v, ct.BS);
+      rpass_sym<DIM, 1>(v, ct.BS);
+      if constexpr (DIM == 3) rpass_sym<DIM, 2>(v, ct.BS);
 #pragma unroll
       for (int q = 0; q < NQ; ++q) xs[q] = v[q];
       T* gs = sG + s * Cfg::SG + c * DIM * NQ;
-      rpass_out<DIM, 0>(v, sDd[0], gs);
-      rpass_out<DIM, 1>(v, sDd[1], gs + NQ);
-      if constexpr (DIM == 3) rpass_out<DIM, 2>(v, sDd[2], gs + 2 * NQ);
+      rpass_out_d<DIM, 0>(v, sDd[0], gs);
+      rpass_out_d<DIM, 1>(v, sDd[1], gs + NQ);
+      if constexpr (DIM == 3) rpass_out_d<DIM, 2>(v, sDd[2], gs + 2 * NQ);
     }
     __syncthreads();
 
@@ -523,12 +578,12 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
             for (int q = 0; q < NQ; ++q) acc[q] = 0;
           }
           const T* gs = sG + s * Cfg::SG + c * DIM * NQ;
-          rpass_acc<DIM, 0>(acc, sDdt[0], gs);
-          rpass_acc<DIM, 1>(acc, sDdt[1], gs + NQ);
-          if constexpr (DIM == 3) rpass_acc<DIM, 2>(acc, sDdt[2], gs + 2 * NQ);
-          rpass<DIM, 0>(acc, ct.Bt);
-          rpass<DIM, 1>(acc, ct.Bt);
-          if constexpr (DIM == 3) rpass<DIM, 2>(acc, ct.Bt);
+          rpass_acc_d<DIM, 0>(acc, sDdt[0], gs);
+          rpass_acc_d<DIM, 1>(acc, sDdt[1], gs + NQ);
+          if constexpr (DIM == 3) rpass_acc_d<DIM, 2>(acc, sDdt[2], gs + 2 * NQ);
+          rpass_sym<DIM, 0>(acc, ct.BtS);
+          rpass_sym<DIM, 1>(acc, ct.BtS);
+          if constexpr (DIM == 3) rpass_sym<DIM, 2>(acc, ct.BtS);
           const int cell = sCell[ci];
           const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
           if constexpr (MODE == OP_RES) {

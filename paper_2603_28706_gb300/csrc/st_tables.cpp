@@ -101,6 +101,19 @@ void make_ref_tables(RefTables& R) {
       }
       R.Dc[q * 3 + j] = s;
     }
+  // The Gauss points are symmetric about 1/2, so B is centro-symmetric and Dc
+  // centro-antisymmetric (zero centre entry) in exact arithmetic; impose both
+  // exactly (the kernels use the symmetry to skip work)
+  for (int i = 0; i < 4; ++i) {
+    const double b = 0.5 * (R.B[i] + R.B[8 - i]);
+    R.B[i] = R.B[8 - i] = b;
+    const double d = 0.5 * (R.Dc[i] - R.Dc[8 - i]);
+    R.Dc[i] = d;
+    R.Dc[8 - i] = -d;
+  }
+  R.Dc[4] = 0.0;
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) R.Bt[a * 3 + q] = R.B[q * 3 + a];
   for (int q = 0; q < 3; ++q) {
     R.B1[q * 2 + 0] = 1.0 - g[q];
     R.B1[q * 2 + 1] = g[q];
