@@ -93,6 +93,48 @@ def profiled_traffic():
     return int(mt.group(1))
 
 
+NEWTON_WORKLOAD = ("3D channel 4x1x1, 128x32x32 hexes, Q2/Q1, dG(1) 2 Radau points, dt=0.01, parabolic Nitsche "
+                   "inflow vbar=1 at x=0, no-slip walls, do-nothing outflow; p=1.5, delta=1e-3, nu=1e-3, "
+                   "nu_inf=1e-4; first slab from rest; modN Newton to |R|_M <= 1e-8 |R0|_M; 3-level V-cycle, "
+                   "2+2 Vanka sweeps")
+
+
+def newton_comparison(st, torch):
+    """Wall time of one globalised modN Newton step (first slab of the channel
+    flow from rest) with the FP32 V-cycle (mixed) and with the FP64 V-cycle,
+    both inside FP64 FGMRES/Newton, to the same relative residual 1e-8."""
+    p = si.config(5, p=1.5, delta=1e-3, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=4, newton_maxit=30)
+    s = si.sizes(p)
+    out = {"workload": NEWTON_WORKLOAD}
+    for name, prec in (("mixed", st.ST_FP32), ("fp64", st.ST_FP64)):
+        prob = st.Problem(p)
+        n = prob.num_dofs()
+        U = torch.zeros(n, dtype=torch.float64, device="cuda")
+        vprev = torch.zeros(s["Mv"], dtype=torch.float64, device="cuda")
+        # untimed: allocation of the hierarchy and workspaces
+        prob.linearize(st.ST_MODN, U)
+        prob.precond_setup(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status, info = prob.newton_step(st.ST_MODN, U, vprev, vcycle_prec=prec, raise_on_fail=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        # the final residual re-evaluated in FP64 by the library
+        R = torch.empty(n, dtype=torch.float64, device="cuda")
+        prob.residual(U, vprev, R=R)
+        rfin = prob.mnorm(R)
+        out[name] = {"seconds": dt, "status": int(status), "newton_iters": info["newton_iters"],
+                     "fgmres_iters": info["fgmres_iters_total"], "patch_rebuilds": info["patch_rebuilds"],
+                     "rel_residual": rfin / info["res_norm_initial"], "dofs": n}
+        prob.close()
+        del U, vprev, R
+        torch.cuda.empty_cache()
+    out["mixed_s"] = out["mixed"]["seconds"]
+    out["fp64_s"] = out["fp64"]["seconds"]
+    out["speedup_mixed_vs_fp64"] = out["fp64_s"] / out["mixed_s"]
+    return out
+
+
 class ClockSampler:
     def __init__(self, index):
         self.index = index
@@ -197,6 +239,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-newton", action="store_true", help="skip the mixed vs FP64 Newton-step comparison")
     args = ap.parse_args()
 
     p, U, dU, vp = si.workload(2)
@@ -295,6 +338,8 @@ def main():
     e2e = {"value": ws * n * len(tangents) * APPLIES / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": len(tangents) * 2 * 8 * n, "d2h_bytes_per_step": len(tangents) * 8 * n}
 
+    newton = None if (args.no_newton or rank != 0) else newton_comparison(st, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -316,6 +361,7 @@ def main():
                                  (8 * 2 * 32768 * 27 * 11 / 1e6),
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
+                "newton": newton,
                 "clocks": clk.summary()}
         print(json.dumps(line))
     prob.close()

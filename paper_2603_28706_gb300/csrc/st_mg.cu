@@ -344,6 +344,124 @@ __global__ void gj_invert_kernel(T* __restrict__ F, int* __restrict__ piv, int N
   }
 }
 
+// The same inversion with the matrix resident in shared memory (it must fit:
+// N^2 elements): one CTA of JG x RP threads per matrix, RP = N rounded up to a
+// warp multiple; thread (jg, i) owns row i of the columns j = jg (mod JG) in
+// the elimination, so its multiplier stays in a register and the pivot-row
+// entry is a shared-memory broadcast.
+template <typename T>
+__global__ void gj_invert_smem_kernel(T* __restrict__ F, int* __restrict__ piv, int N, long count,
+                                      int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char gj_raw[];
+  T* A = reinterpret_cast<T*>(gj_raw);          // N x N, column-major
+  T* s_row = A + (size_t)N * N;                 // scaled pivot row
+  T* s_col = s_row + N;                         // multipliers (column k)
+  __shared__ T w_val[32];
+  __shared__ int w_idx[32];
+  __shared__ int s_piv;
+  const int RP = (N + 31) & ~31, JG = blockDim.x / RP;
+  const int i = threadIdx.x % RP, jg = threadIdx.x / RP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long m = blockIdx.x; m < count; m += gridDim.x) {
+    T* G = F + m * (long)N * N;
+    int* pv = piv + m * N;
+    for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) A[t] = G[t];
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+      // pivot search by the jg == 0 threads (warps 0 .. RP/32-1)
+      if (jg == 0) {
+        T v = (i >= k && i < N) ? fabs(A[(long)k * N + i]) : (T)-1;
+        int vi = i;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ov = __shfl_down_sync(0xffffffffu, v, o);
+          const int oi = __shfl_down_sync(0xffffffffu, vi, o);
+          if (ov > v || (ov == v && oi < vi)) {
+            v = ov;
+            vi = oi;
+          }
+        }
+        if (lane == 0) {
+          w_val[warp] = v;
+          w_idx[warp] = vi;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        T v = w_val[0];
+        int vi = w_idx[0];
+        for (int w = 1; w < RP / 32; ++w)
+          if (w_val[w] > v || (w_val[w] == v && w_idx[w] < vi)) {
+            v = w_val[w];
+            vi = w_idx[w];
+          }
+        s_piv = vi;
+        pv[k] = vi;
+        if (!(v > 0)) atomicExch(err, 1);
+      }
+      __syncthreads();
+      const int p = s_piv;
+      const T d = A[(long)k * N + p];
+      const T inv = d != (T)0 ? (T)1 / d : (T)0;
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const T rk = A[(long)j * N + p];
+        if (p != k) A[(long)j * N + p] = A[(long)j * N + k];
+        s_row[j] = (j == k ? (T)1 : rk) * inv;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < N; r += blockDim.x) s_col[r] = (r == k) ? (T)0 : A[(long)k * N + r];
+      __syncthreads();
+      if (i < N) {
+        const T f = s_col[i];
+        for (int j = jg; j < N; j += JG) {
+          T* aij = A + (long)j * N + i;
+          if (i == k) *aij = s_row[j];
+          else *aij = (j == k ? (T)0 : *aij) - f * s_row[j];
+        }
+      }
+      __syncthreads();
+    }
+    for (int k = N - 1; k >= 0; --k) {
+      const int p = pv[k];
+      if (p != k)
+        for (int r = threadIdx.x; r < N; r += blockDim.x) {
+          const T t = A[(long)k * N + r];
+          A[(long)k * N + r] = A[(long)p * N + r];
+          A[(long)p * N + r] = t;
+        }
+      __syncthreads();
+    }
+    for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) G[t] = A[t];
+    __syncthreads();
+  }
+}
+
+// launch the shared-memory inversion when the matrix fits, else the global one
+template <typename T>
+cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
+  const size_t sm = ((size_t)N * N + 2 * (size_t)N) * sizeof(T);
+  int maxsm = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (sm + 1024 <= (size_t)maxsm) {
+    const int RP = (N + 31) & ~31;
+    const int JG = RP <= 128 ? 4 : (RP <= 512 ? 2 : 1);
+    e = cudaFuncSetAttribute(gj_invert_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int occ = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gj_invert_smem_kernel<T>, JG * RP, sm);
+    if (e != cudaSuccess) return e;
+    const long cap = (long)(occ > 0 ? occ : 1) * nsm;
+    const unsigned g = (unsigned)(count < cap ? count : cap);
+    gj_invert_smem_kernel<T><<<g, JG * RP, sm, st>>>(F, piv, N, count, err);
+  } else {
+    const unsigned g = (unsigned)(count < 8L * nsm ? count : 8L * nsm);
+    gj_invert_kernel<T><<<g, 256, 0, st>>>(F, piv, N, count, err);
+  }
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ Vanka solve
 // For the patches (cells) of one colour class: x = A_K^{-1} defect|_K with the
 // explicit inverse (a matrix-vector product streamed column by column), then
@@ -879,13 +997,13 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
       else patch_assemble<3, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        gj_invert_kernel<double><<<g, 256, 0, h->stream>>>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
+        e = invert_patches<double>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
     } else {
       if (h->dim == 2) patch_assemble<2, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       else patch_assemble<3, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        gj_invert_kernel<float><<<g, 256, 0, h->stream>>>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err);
+        e = invert_patches<float>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
   }

@@ -261,6 +261,79 @@ __device__ __forceinline__ void rpass_acc(T* acc, const MT* m, const T* g) {
   }
 }
 
+// Q1 nodal values (m = mx + 2 my + 4 mz) -> values at the 3^DIM Gauss points
+// (q = qx + 3 qy + 9 qz), one 2 -> 3 pass per direction; B1 is [q][a]
+template <int DIM, typename T, typename MT>
+__device__ __forceinline__ void q1_to_gauss(const T* pn, const MT* B1, T* out) {
+  const T b00 = (T)B1[0], b01 = (T)B1[1], b10 = (T)B1[2], b11 = (T)B1[3], b20 = (T)B1[4], b21 = (T)B1[5];
+  constexpr int NZ = DIM == 3 ? 2 : 1, QZ = DIM == 3 ? 3 : 1;
+  T t1[NZ][2][3], t2[NZ][3][3];
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      const T p0 = pn[2 * y + 4 * z], p1 = pn[1 + 2 * y + 4 * z];
+      t1[z][y][0] = fma(b01, p1, b00 * p0);
+      t1[z][y][1] = fma(b11, p1, b10 * p0);
+      t1[z][y][2] = fma(b21, p1, b20 * p0);
+    }
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      t2[z][0][x] = fma(b01, t1[z][1][x], b00 * t1[z][0][x]);
+      t2[z][1][x] = fma(b11, t1[z][1][x], b10 * t1[z][0][x]);
+      t2[z][2][x] = fma(b21, t1[z][1][x], b20 * t1[z][0][x]);
+    }
+#pragma unroll
+  for (int y = 0; y < 3; ++y)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      if constexpr (DIM == 3) {
+        out[x + 3 * y] = fma(b01, t2[1][y][x], b00 * t2[0][y][x]);
+        out[x + 3 * y + 9] = fma(b11, t2[1][y][x], b10 * t2[0][y][x]);
+        out[x + 3 * y + 18] = fma(b21, t2[1][y][x], b20 * t2[0][y][x]);
+      } else {
+        out[x + 3 * y] = t2[0][y][x];
+      }
+    }
+  (void)QZ;
+}
+
+// transpose of q1_to_gauss: out_m = sum_q psi_m(q) f(q)
+template <int DIM, typename T, typename MT>
+__device__ __forceinline__ void gauss_to_q1(const T* f, const MT* B1, T* out) {
+  const T b00 = (T)B1[0], b01 = (T)B1[1], b10 = (T)B1[2], b11 = (T)B1[3], b20 = (T)B1[4], b21 = (T)B1[5];
+  constexpr int NZ = DIM == 3 ? 2 : 1;
+  T t2[NZ][3][3], t1[NZ][2][3];
+#pragma unroll
+  for (int y = 0; y < 3; ++y)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      if constexpr (DIM == 3) {
+        const T f0 = f[x + 3 * y], f1 = f[x + 3 * y + 9], f2 = f[x + 3 * y + 18];
+        t2[0][y][x] = fma(b20, f2, fma(b10, f1, b00 * f0));
+        t2[1][y][x] = fma(b21, f2, fma(b11, f1, b01 * f0));
+      } else {
+        t2[0][y][x] = f[x + 3 * y];
+      }
+    }
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      t1[z][0][x] = fma(b20, t2[z][2][x], fma(b10, t2[z][1][x], b00 * t2[z][0][x]));
+      t1[z][1][x] = fma(b21, t2[z][2][x], fma(b11, t2[z][1][x], b01 * t2[z][0][x]));
+    }
+#pragma unroll
+  for (int z = 0; z < NZ; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      out[2 * y + 4 * z] = fma(b20, t1[z][y][2], fma(b10, t1[z][y][1], b00 * t1[z][y][0]));
+      out[1 + 2 * y + 4 * z] = fma(b21, t1[z][y][2], fma(b11, t1[z][y][1], b01 * t1[z][y][0]));
+    }
+}
+
 // colour-ordered index of a linear cell id (the coefficient caches use it)
 template <int DIM>
 __device__ __forceinline__ int colour_of(int ex, int ey, int ez) {
@@ -394,8 +467,20 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
     __syncthreads();
 
     // ---- S1: per (slot, component), in registers: values at the Gauss points
-    //      (Q2 basis, one pass per direction), then the gradient in collocation form
-    for (int it = threadIdx.x; it < ns * NC; it += blockDim.x) {
+    //      (Q2 basis, one pass per direction), then the gradient in collocation
+    //      form; per slot: the pressure at the Gauss points (Q1 basis) into sQ
+    constexpr int NPI = (MODE == OP_LIN) ? 0 : 1;  // pressure items per slot
+    for (int it = threadIdx.x; it < ns * (NC + NPI); it += blockDim.x) {
+      if (it >= ns * NC) {
+        const int s = it - ns * NC;
+        T pn[NP], pq[NQ];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) pn[m] = sP[s * NP + m];
+        q1_to_gauss<DIM>(pn, ct.B1, pq);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sQ[s * NQ + q] = pq[q];
+        continue;
+      }
       const int s = it / NC, c = it % NC;
       T* xs = sX + s * Cfg::SX + c * NQ;
       T v[NQ];
@@ -464,11 +549,7 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
         T nuw[3] = {0, 0, 0};
 #pragma unroll
         for (int c = 0; c < NC; ++c) nuw[c] = cp[(2 + NS + c) * NQ];
-        // pressure increment at q
-        const T* psi = (DIM == 3) ? &ct.PSI3[q * 8] : &ct.PSI2[q * 4];
-        T dpi = 0;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) dpi += psi[m] * sP[s * NP + m];
+        const T dpi = sQ[s * NQ + q];  // pressure increment at q (S1)
         const T tw = wq * (T)(a.vol * a.tw[mu]);
         const T pd = -dpi * tw;
         T G[3][3];
@@ -526,10 +607,7 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
           for (int j = 0; j < DIM; ++j) sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = G[c][j];
         sQ[s * NQ + q] = -div * tw;  // pressure test flux
       } else {  // OP_RES: F = RHS - LHS, gradient-test flux -(S(Du) - u (x) u - pi I)
-        const T* psi = (DIM == 3) ? &ct.PSI3[q * 8] : &ct.PSI2[q * 4];
-        T pi = 0;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) pi += psi[m] * sP[s * NP + m];
+        const T pi = sQ[s * NQ + q];  // pressure at q (S1)
         T A[3][3];
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
@@ -559,7 +637,7 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
       // ---- S4: per (slot, component), in registers: K_t (x) M_x value term,
       //      transposed derivative chain, transposed value passes, nodal value
       //      terms (residual), scatter-add; per (slot, pressure node): pressure test
-      for (int it = threadIdx.x; it < ns * (NC + NP); it += blockDim.x) {
+      for (int it = threadIdx.x; it < ns * (NC + 1); it += blockDim.x) {
         if (it < ns * NC) {
           const int s = it / NC, c = it % NC;
           const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
@@ -626,24 +704,29 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
             ob[qx + a.g2[0] * (qy + a.g2[1] * qz)] = acc[q];
           }
         } else {
-          const int r = it - ns * NC;
-          const int s = r / NP, m = r % NP;
+          // pressure test of the slot, sum-factorised (transposed Q1 passes)
+          const int s = it - ns * NC;
           const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
-          T acc = 0;
+          T fq[NQ], pt[NP];
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) acc += ((DIM == 3) ? ct.PSI3[q * 8 + m] : ct.PSI2[q * 4 + m]) * sQ[s * NQ + q];
+          for (int q = 0; q < NQ; ++q) fq[q] = sQ[s * NQ + q];
+          gauss_to_q1<DIM>(fq, ct.B1, pt);
           const int cell = sCell[ci];
           const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
           if constexpr (MODE == OP_ELM) {
             const long item = b0 + s;
             T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
-            E[(long)(NC * NQ + m) * D::NE] = acc;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) E[(long)(NC * NQ + m) * D::NE] = pt[m];
             continue;
           }
-          const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
-          const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
-          reinterpret_cast<T*>(a.cbuf)[(long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
-                                       (long)mu * a.Mp + g] = acc;
+          T* pb = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
+                  (long)mu * a.Mp;
+#pragma unroll
+          for (int m = 0; m < NP; ++m) {
+            const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
+            pb[(ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz))] = pt[m];
+          }
         }
       }
     }
