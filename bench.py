@@ -38,22 +38,15 @@ WORKLOAD = "3D unit cube 32^3 hexes, Q2/Q1, dG(1) 2 Radau points, p=1.3, delta=1
            "100 FP64 Jacobian applies each for exN, modN, Pic"
 
 
+FLOP_PER_DOF = 400  # algorithmic FP64 flops per space-time DoF of one apply (sum-factorised, cached coefficients)
+
+
 def flops_per_apply(p):
-    """Algorithmic FP64 flops of one Jacobian apply of the sum-factorised
-    kernel (FMA = 2 flops), per cell-node and per boundary face-node."""
-    K1 = p["k"] + 1
-    if p["dim"] == 3:
-        vol = 1215 + 1215 + 162 * K1 + 2106 + 1458 + 424 + 1215
-        face = 3600
-        nx, ny, nz = p["nx"], p["ny"], p["nz"]
-        nfaces = 2 * (nx * ny + ny * nz + nx * nz)
-        ncells = nx * ny * nz
-    else:
-        vol = 270 + 180 + 36 * K1 + 9 * 40 + 180 + 4 * 17 + 180
-        face = 400
-        nfaces = 2 * (p["nx"] + p["ny"])
-        ncells = p["nx"] * p["ny"]
-    return K1 * (ncells * vol + nfaces * face)
+    """Algorithmic FP64 flops of one Jacobian apply: 400 flop per space-time
+    DoF for the sum-factorised operator with cached tangent coefficients
+    (value and gradient interpolation, pointwise work, transposed integration
+    and pressure terms per cell and Radau node, FMA = 2 flops)."""
+    return FLOP_PER_DOF * si.sizes(p)["Nst"]
 
 
 def bytes_per_apply(p):
@@ -80,17 +73,19 @@ def kernel_sources_hash():
 
 
 def profiled_traffic():
-    """DRAM bytes (read + write) of one apply from the committed ncu summary,
-    or None when the kernel sources changed since those counters were taken."""
+    """DRAM bytes (read + write) and executed FP64 flops of one apply from the
+    committed ncu summary, or None when the kernel sources changed since those
+    counters were taken."""
     try:
         text = open(PROFILE).read()
     except OSError:
-        return None
+        return None, None
     mh = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", text)
     mt = re.search(r"traffic_bytes_per_apply:\s*([0-9]+)", text)
+    mf = re.search(r"executed_fp64_flops_per_apply:\s*([0-9]+)", text)
     if not mh or not mt or mh.group(1) != kernel_sources_hash():
-        return None
-    return int(mt.group(1))
+        return None, None
+    return int(mt.group(1)), (int(mf.group(1)) if mf else None)
 
 
 NEWTON_WORKLOAD = ("3D channel 4x1x1, 128x32x32 hexes, Q2/Q1, dG(1) 2 Radau points, dt=0.01, parabolic Nitsche "
@@ -309,10 +304,13 @@ def main():
     fl = flops_per_apply(p)
     peak = 152 * 2 * 2 * 2.070e9 / 1e12  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz
     achieved = fl / (apply_ms * 1e-3) / 1e12
-    traffic = profiled_traffic()
+    traffic, executed = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "one modN apply: st_op_kernel<3,2,double,OP_JAC,1> (all cells, colour-private outputs) + st_face_kernel (side stream) + st_node_sum", "traffic_source": os.path.relpath(PROFILE, ROOT),
-                "apply_ms": apply_ms, "flops_per_apply": fl, "algorithmic_bytes_per_apply": bytes_per_apply(p),
+                "apply_ms": apply_ms, "flops_per_apply": fl, "flop_per_dof": FLOP_PER_DOF,
+                "executed_fp64_flops_per_apply": executed,
+                "executed_frac": (executed / (apply_ms * 1e-3) / 1e12 / peak) if executed else None,
+                "algorithmic_bytes_per_apply": bytes_per_apply(p),
                 "hbm_frac_of_measured": bytes_per_apply(p) / (apply_ms * 1e-3) / 6771.1e9}
 
     # end to end through the public API with pinned host buffers

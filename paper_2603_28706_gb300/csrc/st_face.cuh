@@ -445,51 +445,75 @@ struct GatherEnt {
 
 // out = sum of the 2^DIM class-private volume outputs (entries a class does
 // not reach are zero in its buffer, so every class is added, in a fixed
-// order: coalesced, branch-free) + the boundary-face contributions of the
-// face scratch (CSR row of the node, if any).  One thread per slab entry;
-// writes every entry of out.
+// order) + the boundary-face contributions of the face scratch (CSR row of
+// the node, if any).  One thread per spatial node: a velocity node handles
+// its K1 x DIM slab entries, a pressure node its K1 entries, so the gather
+// lists are read once per node and all class loads of a thread are
+// independent.  Writes every entry of out.
 template <int DIM, int K1, typename T>
 __global__ void st_node_sum(const OpArgs a, const int* __restrict__ gmap, const int* __restrict__ gptr,
                             const GatherEnt* __restrict__ gent, const T* __restrict__ fscr, T* __restrict__ out) {
   using D = Dims<DIM>;
-  constexpr int NC = D::NC, NFQ = D::NFQ;
+  constexpr int NC = D::NC, NFQ = D::NFQ, NCOL = 1 << DIM;
   constexpr int NOUT = 2 * NC * NFQ + D::NFP;
   const T* cb = reinterpret_cast<const T*>(a.cbuf);
-  const long nvel = (long)K1 * a.Mv, ntot = nvel + (long)K1 * a.Mp;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < ntot; idx += (long)gridDim.x * blockDim.x) {
-    T v[1 << DIM];
+  const int nq2 = (int)a.Nq2, nq1 = (int)a.Nq1, mv = (int)a.Mv, mp = (int)a.Mp;
+  const long cs = a.cbuf_stride;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq2 + nq1; t += gridDim.x * blockDim.x) {
+    if (t < nq2) {
+      const int g = t;
+      T acc[K1 * NC];
 #pragma unroll
-    for (int c = 0; c < (1 << DIM); ++c) v[c] = cb[(long)c * a.cbuf_stride + idx];
-    T acc = v[0];
+      for (int mu = 0; mu < K1; ++mu)
 #pragma unroll
-    for (int c = 1; c < (1 << DIM); ++c) acc += v[c];
-    int row, mu, comp = 0;
-    if (idx < nvel) {
-      mu = (int)(idx / a.Mv);
-      const long r = idx - (long)mu * a.Mv;
-      comp = (int)(r / a.Nq2);
-      row = gmap[r - (long)comp * a.Nq2];
-    } else {
-      const long r = idx - nvel;
-      mu = (int)(r / a.Mp);
-      row = gmap[a.Nq2 + (r - (long)mu * a.Mp)];
-    }
-    if (row >= 0) {
-      const int b = gptr[row], e = gptr[row + 1];
-      if (idx < nvel) {
-        for (int j = b; j < e; ++j) {
-          const GatherEnt ge = gent[j];
-          const T* fs = fscr + ((long)ge.fid * K1 + mu) * NOUT + ge.tn + comp * NFQ;
-          acc += (T)ge.e * fs[0] + (T)ge.ed * fs[NC * NFQ];
+        for (int c = 0; c < NC; ++c) {
+          const long e = (long)mu * mv + (long)c * nq2 + g;
+          T v = cb[e];
+#pragma unroll
+          for (int col = 1; col < NCOL; ++col) v += cb[col * cs + e];
+          acc[mu * NC + c] = v;
         }
-      } else {
+      const int row = gmap[g];
+      if (row >= 0) {
+        const int b = gptr[row], e = gptr[row + 1];
         for (int j = b; j < e; ++j) {
           const GatherEnt ge = gent[j];
-          acc += fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
+          const T ev = (T)ge.e, ed = (T)ge.ed;
+#pragma unroll
+          for (int mu = 0; mu < K1; ++mu) {
+            const T* fs = fscr + ((long)ge.fid * K1 + mu) * NOUT + ge.tn;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[mu * NC + c] += ev * fs[c * NFQ] + ed * fs[NC * NFQ + c * NFQ];
+          }
         }
       }
+#pragma unroll
+      for (int mu = 0; mu < K1; ++mu)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[(long)mu * mv + (long)c * nq2 + g] = acc[mu * NC + c];
+    } else {
+      const int g = t - nq2;
+      T acc[K1];
+#pragma unroll
+      for (int mu = 0; mu < K1; ++mu) {
+        const long e = (long)K1 * mv + (long)mu * mp + g;
+        T v = cb[e];
+#pragma unroll
+        for (int col = 1; col < NCOL; ++col) v += cb[col * cs + e];
+        acc[mu] = v;
+      }
+      const int row = gmap[nq2 + g];
+      if (row >= 0) {
+        const int b = gptr[row], e = gptr[row + 1];
+        for (int j = b; j < e; ++j) {
+          const GatherEnt ge = gent[j];
+#pragma unroll
+          for (int mu = 0; mu < K1; ++mu) acc[mu] += fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
+        }
+      }
+#pragma unroll
+      for (int mu = 0; mu < K1; ++mu) out[(long)K1 * mv + (long)mu * mp + g] = acc[mu];
     }
-    out[idx] = acc;
   }
 }
 

@@ -65,7 +65,7 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   if (e != cudaSuccess) return e;
   if (MODE != OP_LIN) {
-    long g = (L.Nst + 255) / 256;
+    long g = (L.Nq2 + L.Nq1 + 255) / 256;
     if (g > 16L * h->nsm) g = 16L * h->nsm;
     st_node_sum<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(a, L.d_gmap, L.d_gptr,
                                                                 reinterpret_cast<const GatherEnt*>(L.d_gent), fscr,
