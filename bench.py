@@ -94,14 +94,18 @@ NEWTON_WORKLOAD = ("3D channel 4x1x1, 128x32x32 hexes, Q2/Q1, dG(1) 2 Radau poin
                    "2+2 Vanka sweeps")
 
 
-def newton_comparison(st, torch):
+def newton_comparison(st, torch, mesh=(128, 32, 32), arms=("mixed", "fp64")):
     """Wall time of one globalised modN Newton step (first slab of the channel
     flow from rest) with the FP32 V-cycle (mixed) and with the FP64 V-cycle,
     both inside FP64 FGMRES/Newton, to the same relative residual 1e-8."""
-    p = si.config(5, p=1.5, delta=1e-3, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=4, newton_maxit=30)
+    p = si.config(5, nx=mesh[0], ny=mesh[1], nz=mesh[2], p=1.5, delta=1e-3, tol_rel=1e-8, tol_abs=1e-30,
+                  coarse_sweeps=4, newton_maxit=30)
     s = si.sizes(p)
-    out = {"workload": NEWTON_WORKLOAD}
-    for name, prec in (("mixed", st.ST_FP32), ("fp64", st.ST_FP64)):
+    out = {"workload": NEWTON_WORKLOAD if tuple(mesh) == (128, 32, 32) else
+           NEWTON_WORKLOAD.replace("128x32x32", "%dx%dx%d" % tuple(mesh))}
+    precs = {"mixed": st.ST_FP32, "fp64": st.ST_FP64}
+    for name in arms:
+        prec = precs[name]
         prob = st.Problem(p)
         n = prob.num_dofs()
         U = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -124,9 +128,10 @@ def newton_comparison(st, torch):
         prob.close()
         del U, vprev, R
         torch.cuda.empty_cache()
-    out["mixed_s"] = out["mixed"]["seconds"]
-    out["fp64_s"] = out["fp64"]["seconds"]
-    out["speedup_mixed_vs_fp64"] = out["fp64_s"] / out["mixed_s"]
+    if "mixed" in out and "fp64" in out:
+        out["mixed_s"] = out["mixed"]["seconds"]
+        out["fp64_s"] = out["fp64"]["seconds"]
+        out["speedup_mixed_vs_fp64"] = out["fp64_s"] / out["mixed_s"]
     return out
 
 
@@ -235,6 +240,9 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the mixed vs FP64 Newton-step comparison")
+    ap.add_argument("--newton-only", action="store_true", help="run only the Newton-step comparison and print it")
+    ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
+    ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     args = ap.parse_args()
 
     p, U, dU, vp = si.workload(2)
@@ -249,6 +257,9 @@ def main():
         dist.init_process_group("nccl")
     import paper_2603_28706_gb300 as st
     st.build.build()
+    if args.newton_only:
+        print(json.dumps(newton_comparison(st, torch, tuple(args.newton_mesh), tuple(args.newton_arms.split(",")))))
+        return
     stream = torch.cuda.current_stream()
     prob = st.Problem(p, stream=stream)
     n = prob.num_dofs()
@@ -336,7 +347,7 @@ def main():
     e2e = {"value": ws * n * len(tangents) * APPLIES / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": len(tangents) * 2 * 8 * n, "d2h_bytes_per_step": len(tangents) * 8 * n}
 
-    newton = None if (args.no_newton or rank != 0) else newton_comparison(st, torch)
+    newton = None if (args.no_newton or rank != 0) else newton_comparison(st, torch, tuple(args.newton_mesh))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
