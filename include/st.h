@@ -203,6 +203,45 @@ const char* st_last_error(const st_problem* h);
  * overlap on the GPU race and must be serialised by the caller. */
 st_status st_mnorm_noalloc(const st_params* params, void* cuda_stream, const double* r, double* out);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent slab problems solved side by side: each instance has its
+ * own mesh, parameters and state (Sec. 3 and 6 per instance); all instances
+ * share dim and k (one kernel instantiation).  The operator calls run the
+ * volume terms of every instance in one persistent launch whose work queue
+ * holds (instance, cell batch) items, so instances of uneven size keep all SMs
+ * busy; the face terms and the node sums follow per instance.  Vector
+ * arguments are host arrays of n caller-owned device pointers (instance i:
+ * the layout and dtype of the single-problem calls).  Calls are enqueued on
+ * `cuda_stream`; the batch owns its instances. */
+typedef struct st_batch st_batch;
+
+/* n instances from params[0..n-1] (n >= 1).  ST_EINVAL if a parameter block
+ * is invalid or dim / k differ between instances. */
+st_status st_batch_setup(const st_params* params, int n, void* cuda_stream, st_batch** out);
+st_status st_batch_destroy(st_batch* b);
+/* Space-time dofs of instance i (0 for a bad index). */
+size_t st_batch_num_dofs(const st_batch* b, int i);
+
+/* st_linearize for every instance at its state U[i] (FP64). */
+st_status st_batch_linearize(st_batch* b, st_tangent tangent, const void* const* U);
+/* out[i] = J_i dU[i] for every instance (the linearisation of st_batch_linearize
+ * with the same tangent; ST_EINVAL otherwise). */
+st_status st_batch_jacobian_apply(st_batch* b, st_tangent tangent, st_prec prec, const void* const* dU,
+                                  void* const* out);
+/* R[i] = R_n(U[i]) with data v_prev[i] and f[i] (f may be NULL: all forcings
+ * zero; an entry may be NULL: that instance's forcing is zero). */
+st_status st_batch_residual(st_batch* b, st_prec prec, const void* const* U, const void* const* v_prev,
+                            const void* const* f, void* const* R);
+/* st_newton_step for every instance, the instances driven concurrently (one
+ * host thread and one internal CUDA stream each); U[i] updated in place,
+ * info[i] filled (info may be NULL).  Synchronous.  Returns ST_OK when every
+ * instance converged, else the status of the first instance that did not
+ * (the others still complete). */
+st_status st_batch_newton_step(st_batch* b, st_tangent tangent, st_prec vcycle_prec, void* const* U,
+                               const void* const* v_prev, const void* const* f, st_newton_info* info);
+/* Message describing the last failure on b (never NULL). */
+const char* st_batch_last_error(const st_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

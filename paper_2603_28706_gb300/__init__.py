@@ -20,7 +20,8 @@ STATUS = {0: "ST_OK", 1: "ST_EINVAL", 2: "ST_ECUDA", 3: "ST_ENOMEM", 4: "ST_NOT_
 
 EXPORTED = ["st_setup_mesh", "st_destroy", "st_num_dofs", "st_residual", "st_linearize", "st_jacobian_apply",
             "st_mnorm", "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step", "st_last_error",
-            "st_mnorm_noalloc"]
+            "st_mnorm_noalloc", "st_batch_setup", "st_batch_destroy", "st_batch_num_dofs", "st_batch_linearize",
+            "st_batch_jacobian_apply", "st_batch_residual", "st_batch_newton_step", "st_batch_last_error"]
 
 
 class StParams(ctypes.Structure):
@@ -88,6 +89,20 @@ def load(build_if_missing=True):
     lib.st_last_error.restype = ctypes.c_char_p
     lib.st_mnorm_noalloc.argtypes = [P, vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.st_mnorm_noalloc.restype = ctypes.c_int
+    vpp = ctypes.POINTER(vp)
+    lib.st_batch_setup.argtypes = [P, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.st_batch_destroy.argtypes = [vp]
+    lib.st_batch_num_dofs.argtypes = [vp, ctypes.c_int]
+    lib.st_batch_num_dofs.restype = ctypes.c_size_t
+    lib.st_batch_linearize.argtypes = [vp, ctypes.c_int, vpp]
+    lib.st_batch_jacobian_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, vpp, vpp]
+    lib.st_batch_residual.argtypes = [vp, ctypes.c_int, vpp, vpp, vpp, vpp]
+    lib.st_batch_newton_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, vpp, vpp, vpp, ctypes.POINTER(StNewtonInfo)]
+    lib.st_batch_last_error.argtypes = [vp]
+    lib.st_batch_last_error.restype = ctypes.c_char_p
+    for name in ("st_batch_setup", "st_batch_destroy", "st_batch_linearize", "st_batch_jacobian_apply",
+                 "st_batch_residual", "st_batch_newton_step"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in EXPORTED:
         getattr(lib, name)
     for name in ("st_setup_mesh", "st_destroy", "st_residual", "st_linearize", "st_jacobian_apply", "st_mnorm",
@@ -258,3 +273,111 @@ class Problem:
         if raise_on_fail and st not in (ST_OK,):
             raise StError(st, "st_newton_step: %s" % self.lib.st_last_error(self.h).decode())
         return st, {name: getattr(info, name) for name, _ in StNewtonInfo._fields_}
+
+
+def _ptr_array(ts, dtype, sizes, name):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t, dtype, sizes[i], "%s[%d]" % (name, i)).value
+    return arr
+
+
+class Batch:
+    """Independent slab problems (same dim and k) handled together (st_batch_*):
+    the operator calls share one persistent volume launch over all instances'
+    cells; Newton steps run concurrently, one host thread and stream each."""
+
+    def __init__(self, plist, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU path)")
+        self.lib = load()
+        self.plist = [dict(p) for p in plist]
+        arr = (StParams * len(plist))(*[params(p) for p in plist])
+        self._arr = arr
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        b = ctypes.c_void_p()
+        st = self.lib.st_batch_setup(arr, len(plist), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(b))
+        if st != ST_OK:
+            raise StError(st, "st_batch_setup failed")
+        self.b = b
+        self.n = len(plist)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.st_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != ST_OK:
+            raise StError(st, "%s: %s" % (what, self.lib.st_batch_last_error(self.b).decode()))
+        return st
+
+    def num_dofs(self, i):
+        return int(self.lib.st_batch_num_dofs(self.b, i))
+
+    def velocity_size(self, i):
+        p = self.plist[i]
+        g = 1
+        for a, key in enumerate(("nx", "ny", "nz")[:p["dim"]]):
+            g *= 2 * p[key] + 1
+        return p["dim"] * g
+
+    # -- entry points (same names as the C ABI) --
+    def linearize(self, tangent, Us):
+        import torch
+        self._check(self.lib.st_batch_linearize(
+            self.b, tangent, _ptr_array(Us, torch.float64, [self.num_dofs(i) for i in range(self.n)], "U")),
+            "st_batch_linearize")
+
+    def jacobian_apply(self, tangent, dUs, outs=None, prec=ST_FP64):
+        import torch
+        dt = _prec_dtype(prec)
+        if outs is None:
+            outs = [torch.empty(self.num_dofs(i), dtype=dt, device=dUs[i].device) for i in range(self.n)]
+        sz = [self.num_dofs(i) for i in range(self.n)]
+        self._check(self.lib.st_batch_jacobian_apply(self.b, tangent, prec, _ptr_array(dUs, dt, sz, "dU"),
+                                                     _ptr_array(outs, dt, sz, "out")), "st_batch_jacobian_apply")
+        return outs
+
+    def residual(self, Us, v_prevs, fs=None, Rs=None, prec=ST_FP64):
+        import torch
+        dt = _prec_dtype(prec)
+        if Rs is None:
+            Rs = [torch.empty(self.num_dofs(i), dtype=dt, device=Us[i].device) for i in range(self.n)]
+        sz = [self.num_dofs(i) for i in range(self.n)]
+        vs = [self.velocity_size(i) for i in range(self.n)]
+        fa = None
+        if fs is not None:
+            fa = (ctypes.c_void_p * self.n)()
+            for i, f in enumerate(fs):
+                fa[i] = None if f is None else _ptr(f, dt, (self.plist[i]["k"] + 1) * vs[i], "f[%d]" % i).value
+        self._check(self.lib.st_batch_residual(self.b, prec, _ptr_array(Us, dt, sz, "U"),
+                                               _ptr_array(v_prevs, dt, vs, "v_prev"), fa,
+                                               _ptr_array(Rs, dt, sz, "R")), "st_batch_residual")
+        return Rs
+
+    def newton_step(self, tangent, Us, v_prevs, fs=None, vcycle_prec=ST_FP32, raise_on_fail=True):
+        import torch
+        infos = (StNewtonInfo * self.n)()
+        sz = [self.num_dofs(i) for i in range(self.n)]
+        vs = [self.velocity_size(i) for i in range(self.n)]
+        fa = None
+        if fs is not None:
+            fa = (ctypes.c_void_p * self.n)()
+            for i, f in enumerate(fs):
+                fa[i] = None if f is None else _ptr(f, torch.float64, (self.plist[i]["k"] + 1) * vs[i],
+                                                    "f[%d]" % i).value
+        st = self.lib.st_batch_newton_step(self.b, tangent, vcycle_prec, _ptr_array(Us, torch.float64, sz, "U"),
+                                           _ptr_array(v_prevs, torch.float64, vs, "v_prev"), fa, infos)
+        if raise_on_fail and st != ST_OK:
+            raise StError(st, "st_batch_newton_step: %s" % self.lib.st_batch_last_error(self.b).decode())
+        return st, [{name: getattr(infos[i], name) for name, _ in StNewtonInfo._fields_} for i in range(self.n)]

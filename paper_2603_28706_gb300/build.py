@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libst.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-CU = ["st_api.cu", "st_blas.cu", "st_op2d.cu", "st_op3d.cu", "st_mg.cu", "st_solver.cu"]
+CU = ["st_api.cu", "st_blas.cu", "st_op2d.cu", "st_op3d.cu", "st_mg.cu", "st_solver.cu", "st_batch.cu"]
 CPP = ["st_tables.cpp"]
 
 
@@ -68,7 +68,7 @@ def build(force=False, verbose=False, ptxas_info=False):
         for _, err in res:
             sys.stderr.write(err)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))

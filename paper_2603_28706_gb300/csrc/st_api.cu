@@ -288,6 +288,20 @@ void fill_op_args(const st_problem* h, int level, OpArgs& a) {
     for (int d = 0; d < 3; ++d) a.cn_all[c][d] = L.cn[c][d];
 }
 
+void prepare_op_args(const st_problem* h, int level, int prec, int tangent, const void* in, void* out,
+                     const void* vprev, const void* f, OpArgs& a) {
+  fill_op_args(h, level, a);
+  a.tangent = tangent;
+  a.in = in;
+  a.out = out;
+  a.vprev = vprev;
+  a.f = f;
+  a.cache = prec == ST_FP64 ? (const void*)h->d_cache64 : (const void*)h->d_cache32;
+  a.fcache = prec == ST_FP64 ? (const void*)h->d_fcache64 : (const void*)h->d_fcache32;
+  a.wcache = h->d_cache64;
+  a.wfcache = h->d_fcache64;
+}
+
 cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent, const void* in, void* out,
                       const void* vprev, const void* f) {
   OpArgs a;

@@ -85,6 +85,14 @@ struct OpArgs {
 
 enum OpMode { OP_LIN = 0, OP_JAC = 1, OP_RES = 2, OP_ELM = 3 };
 
+// device scratch of a batched launch (st_batch.cu)
+struct BatchDev {
+  OpArgs* d_desc = nullptr;   // per-instance argument blocks
+  long* d_first = nullptr;    // first work item of every instance (n + 1)
+  unsigned* d_queue = nullptr;
+  int nsm = 0;
+};
+
 template <int DIM> struct Dims {
   static constexpr int NQ = DIM == 3 ? 27 : 9;
   static constexpr int NC = DIM;
@@ -158,6 +166,13 @@ namespace st {
 // operator launches (st_operator_*.cu)
 cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent, const void* in, void* out,
                       const void* vprev, const void* f);
+// argument block of one operator launch on `level` (the data pointers included)
+void prepare_op_args(const st_problem* h, int level, int prec, int tangent, const void* in, void* out,
+                     const void* vprev, const void* f, OpArgs& a);
+cudaError_t dispatch_op_batch_2d(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, int mode, int prec,
+                                 int tangent, cudaStream_t st);
+cudaError_t dispatch_op_batch_3d(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, int mode, int prec,
+                                 int tangent, cudaStream_t st);
 void fill_op_args(const st_problem* h, int level, OpArgs& a);
 
 st_status set_error(st_problem* h, st_status s, const std::string& msg);

@@ -9,6 +9,10 @@ cudaError_t dispatch_elm_2d(const st_problem* h, const Level& L, const OpArgs& a
                            const int* bcells, int nbc) {
   return dispatch_elm_dim<2>(h, L, a, prec, tangent, E, bcells, nbc);
 }
+cudaError_t dispatch_op_batch_2d(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, int mode, int prec,
+                                 int tangent, cudaStream_t st) {
+  return dispatch_op_batch_dim<2>(P, A, n, bd, mode, prec, tangent, st);
+}
 cudaError_t upload_consts_2d(const ConstTables& t, const ConstTablesF& tf) {
   cudaError_t e = cudaMemcpyToSymbol(cT, &t, sizeof(t));
   if (e != cudaSuccess) return e;

@@ -1,54 +1,79 @@
 // Launch helpers for the operator kernels of one dimension.
 #pragma once
 
+#include <vector>
+
 #include "st_face.cuh"
 #include "st_operator.cuh"
 
 namespace st {
 
+// occupancy of a kernel (computed once per instantiation, thread-safe)
+template <typename K>
+int occupancy_once(K kern, int threads, size_t smem) {
+  int occ = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) return 0;
+  return occ < 1 ? 1 : occ;
+}
+
+// all boundary faces of one problem, one launch, writing the face scratch
+// (or, when linearising, the face caches)
 template <int DIM, int K1, typename T, int MODE, int TAN>
-cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
-  using Cfg = OpCfg<DIM, K1, T>;
+cudaError_t launch_faces_t(const st_problem* h, const Level& L, const OpArgs& a, cudaStream_t st) {
   using FCfg = FaceCfg<DIM, T>;
-  auto kern = st_op_kernel<DIM, K1, T, MODE, TAN>;
   auto fkern = st_face_kernel<DIM, K1, T, MODE, TAN>;
-  static int occ = 0, focc = 0;
-  if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FCfg::smem_bytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::NT, Cfg::smem_bytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fkern, OP_THREADS, FCfg::smem_bytes);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-    if (focc < 1) focc = 1;
-  }
-  // The face kernel (all boundary faces, one launch) runs on an internal
-  // stream concurrently with the volume kernel; it writes only the face
-  // scratch (or, when linearising, the face cache).  The volume kernel (one
-  // launch over all cells in colour order) writes every cell's contributions
-  // into the private buffer of its colour class with plain stores.  The
-  // caller's stream then waits for the face kernel and st_node_sum forms
-  // out = sum of the class buffers + face contributions, one thread per entry.
-  cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
-  if (e != cudaSuccess) return e;
-  T* fscr = reinterpret_cast<T*>(h->d_fscr);
+  static const int focc = occupancy_once(fkern, OP_THREADS, FCfg::smem_bytes);
+  if (focc == 0) return cudaErrorInvalidConfiguration;
   const long nslots = L.nfaces * K1;
-  if (nslots > 0) {
-    long fgrid = (nslots + FCfg::FS - 1) / FCfg::FS;
-    const long fcap = 8L * h->nsm;
-    if (fgrid > fcap) fgrid = fcap;
-    fkern<<<(unsigned)fgrid, OP_THREADS, FCfg::smem_bytes, h->s_face>>>(a, L.d_face_cell, L.d_face_side, nslots,
-                                                                         fscr);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  if (nslots == 0) return cudaSuccess;
+  long fgrid = (nslots + FCfg::FS - 1) / FCfg::FS;
+  const long fcap = 8L * h->nsm;
+  if (fgrid > fcap) fgrid = fcap;
+  fkern<<<(unsigned)fgrid, OP_THREADS, FCfg::smem_bytes, st>>>(a, L.d_face_cell, L.d_face_side, nslots,
+                                                                reinterpret_cast<T*>(h->d_fscr));
+  return cudaGetLastError();
+}
+
+// out = sum of the class buffers + face contributions (one thread per node)
+template <int DIM, int K1, typename T>
+cudaError_t launch_node_sum_t(const st_problem* h, const Level& L, const OpArgs& a, cudaStream_t st) {
+  long g = (L.Nq2 + L.Nq1 + 255) / 256;
+  if (g > 16L * h->nsm) g = 16L * h->nsm;
+  st_node_sum<DIM, K1, T><<<(unsigned)g, 256, 0, st>>>(a, L.d_gmap, L.d_gptr,
+                                                       reinterpret_cast<const GatherEnt*>(L.d_gent),
+                                                       reinterpret_cast<const T*>(h->d_fscr),
+                                                       reinterpret_cast<T*>(a.out));
+  return cudaGetLastError();
+}
+
+// the volume kernel's view of the whole finest level
+template <typename T>
+void set_volume_args(const st_problem* h, const Level& L, OpArgs& a) {
   a.col_start = 0;
   a.ncol = L.ncells;
   a.cbuf = sizeof(T) == 8 ? h->d_cbuf64 : h->d_cbuf32;
   a.cbuf_stride = L.Nst;
+}
+
+template <int DIM, int K1, typename T, int MODE, int TAN>
+cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
+  using Cfg = OpCfg<DIM, K1, T>;
+  auto kern = st_op_kernel<DIM, K1, T, MODE, TAN>;
+  static const int occ = occupancy_once(kern, Cfg::NT, Cfg::smem_bytes);
+  if (occ == 0) return cudaErrorInvalidConfiguration;
+  // The face kernel (all boundary faces, one launch) is enqueued on an
+  // internal stream beside the volume kernel; it writes only the face
+  // scratch (or, when linearising, the face cache).  The volume kernel (one
+  // launch over all cells in colour order) writes every cell's contributions
+  // into the private buffer of its colour class with plain stores.  The
+  // caller's stream then waits for the face kernel and st_node_sum forms
+  // out = sum of the class buffers + face contributions, one thread per node.
+  cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_faces_t<DIM, K1, T, MODE, TAN>(h, L, a, h->s_face);
+  if (e != cudaSuccess) return e;
+  set_volume_args<T>(h, L, a);
   {
     // every resident CTA slot gets an equal share of the cells when there are
     // at least half a batch per slot; smaller meshes use full batches
@@ -64,15 +89,69 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   e = cudaEventRecord(h->ev_join, h->s_face);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   if (e != cudaSuccess) return e;
-  if (MODE != OP_LIN) {
-    long g = (L.Nq2 + L.Nq1 + 255) / 256;
-    if (g > 16L * h->nsm) g = 16L * h->nsm;
-    st_node_sum<DIM, K1, T><<<(unsigned)g, 256, 0, h->stream>>>(a, L.d_gmap, L.d_gptr,
-                                                                reinterpret_cast<const GatherEnt*>(L.d_gent), fscr,
-                                                                reinterpret_cast<T*>(a.out));
-    e = cudaGetLastError();
-  }
+  if (MODE != OP_LIN) e = launch_node_sum_t<DIM, K1, T>(h, L, a, h->stream);
   return e;
+}
+
+// Several problems (same dim and k) in one persistent volume launch over the
+// (instance, cell batch) items; faces and node sums per instance on `st`.
+// A[i]: argument block of instance i (fill_op_args + data pointers).
+template <int DIM, int K1, typename T, int MODE, int TAN>
+cudaError_t launch_op_batch_t(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, cudaStream_t st) {
+  using Cfg = OpCfg<DIM, K1, T>;
+  auto kern = st_op_kernel_batch<DIM, K1, T, MODE, TAN>;
+  static const int occ = occupancy_once(kern, Cfg::NT, Cfg::smem_bytes);
+  if (occ == 0) return cudaErrorInvalidConfiguration;
+  std::vector<long> first(n + 1, 0);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const Level& L = P[i]->lev.back();
+    set_volume_args<T>(P[i], L, A[i]);
+    first[i + 1] = first[i] + (L.ncells + Cfg::C - 1) / Cfg::C;
+    e = launch_faces_t<DIM, K1, T, MODE, TAN>(P[i], L, A[i], st);
+  }
+  if (e != cudaSuccess) return e;
+  // pageable host sources: the copies are staged before they return
+  e = cudaMemcpyAsync(bd.d_desc, A, (size_t)n * sizeof(OpArgs), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bd.d_first, first.data(), (size_t)(n + 1) * sizeof(long), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bd.d_queue, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const long cap = (long)occ * bd.nsm;
+  const long grid = first[n] < cap ? (first[n] > 0 ? first[n] : 1) : cap;
+  kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, st>>>(bd.d_desc, bd.d_first, n, bd.d_queue);
+  e = cudaGetLastError();
+  for (int i = 0; i < n && e == cudaSuccess && MODE != OP_LIN; ++i)
+    e = launch_node_sum_t<DIM, K1, T>(P[i], P[i]->lev.back(), A[i], st);
+  return e;
+}
+
+template <int DIM, int K1>
+cudaError_t dispatch_op_batch_k(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, int mode, int prec,
+                                int tangent, cudaStream_t st) {
+  if (mode == OP_LIN) return launch_op_batch_t<DIM, K1, double, OP_LIN, 0>(P, A, n, bd, st);
+  const bool r1 = tangent != ST_PIC;
+  if (mode == OP_JAC) {
+    if (prec == ST_FP64)
+      return r1 ? launch_op_batch_t<DIM, K1, double, OP_JAC, 1>(P, A, n, bd, st)
+                : launch_op_batch_t<DIM, K1, double, OP_JAC, 0>(P, A, n, bd, st);
+    return r1 ? launch_op_batch_t<DIM, K1, float, OP_JAC, 1>(P, A, n, bd, st)
+              : launch_op_batch_t<DIM, K1, float, OP_JAC, 0>(P, A, n, bd, st);
+  }
+  if (prec == ST_FP64) return launch_op_batch_t<DIM, K1, double, OP_RES, 0>(P, A, n, bd, st);
+  return launch_op_batch_t<DIM, K1, float, OP_RES, 0>(P, A, n, bd, st);
+}
+
+template <int DIM>
+cudaError_t dispatch_op_batch_dim(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, int mode, int prec,
+                                  int tangent, cudaStream_t st) {
+  switch (P[0]->K1) {
+    case 1: return dispatch_op_batch_k<DIM, 1>(P, A, n, bd, mode, prec, tangent, st);
+    case 2: return dispatch_op_batch_k<DIM, 2>(P, A, n, bd, mode, prec, tangent, st);
+    case 3: return dispatch_op_batch_k<DIM, 3>(P, A, n, bd, mode, prec, tangent, st);
+    case 4: return dispatch_op_batch_k<DIM, 4>(P, A, n, bd, mode, prec, tangent, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int DIM, int K1>
@@ -112,14 +191,9 @@ cudaError_t launch_elm_t(const st_problem* h, const Level& L, OpArgs a, T* E, co
   auto fkern = st_face_matrix<DIM, K1, T, TAN>;
   constexpr int NE = Dims<DIM>::NE;
   const size_t fsm = (size_t)NE * FCfg::per_slot * sizeof(T) + 64;
-  static int occ = 0;
-  if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem_bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::NT, Cfg::smem_bytes);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-  }
+  static const int occ = occupancy_once(kern, Cfg::NT, Cfg::smem_bytes);
+  static const int focc = occupancy_once(fkern, OP_THREADS, fsm);
+  if (occ == 0 || focc == 0) return cudaErrorInvalidConfiguration;
   a.out = E;
   a.ncol = L.ncells * NE;
   a.col_start = 0;

@@ -363,22 +363,364 @@ struct OpCfg {
   static constexpr size_t smem_bytes = (size_t)S * per_slot * sizeof(T) + (size_t)S * sizeof(int) + 64;
 };
 
+// One batch of the volume kernel: nc items (cells in colour order; element-
+// matrix mode: (cell, column) pairs) starting at b0, in the CTA's shared
+// memory; sDd/sDdt/sM1 hold the scaled 1D matrices of the mesh of `a`.
 template <int DIM, int K1, typename T, int MODE, int TAN>
-__global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpArgs a) {
+__device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const int nc, unsigned char* smem_raw,
+                                         const T (*sDd)[9], const T (*sDdt)[9], const T (*sM1)[9]) {
   using D = Dims<DIM>;
   using Cfg = OpCfg<DIM, K1, T>;
   constexpr int NQ = D::NQ, NC = D::NC, NP = D::NP, NS = D::NS;
-  constexpr int C = Cfg::C, S = Cfg::S;
+  constexpr int S = Cfg::S;
   const auto& ct = CT<T>::t();
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sX = reinterpret_cast<T*>(smem_raw);
   T* sG = sX + S * Cfg::SX;
   T* sP = sG + S * Cfg::SG;
   T* sQ = sP + S * Cfg::SP;
   int* sCell = reinterpret_cast<int*>(sQ + S * Cfg::SQ);  // linear cell id of batch cell
-
   const T* in = reinterpret_cast<const T*>(a.in);
+  constexpr int SK = (MODE == OP_ELM) ? 1 : K1;  // slots per batch item
+  const int ns = nc * SK;
+  (void)NS;
+
+  // ---- batch setup: cell ids (element-matrix mode: item = (cell, column))
+  for (int ci = threadIdx.x; ci < nc; ci += blockDim.x) {
+    if constexpr (MODE == OP_ELM) {
+      sCell[ci] = (int)((b0 + ci) / D::NE);
+    } else {
+      // colour-ordered cell index -> colour class c -> cell (o + 2 i, ...)
+      long li = b0 + ci;
+      int c = 0;
+#pragma unroll
+      for (int cc = 1; cc < (1 << DIM); ++cc) c += (li >= a.col_start_all[cc]) ? 1 : 0;
+      li -= a.col_start_all[c];
+      const int cn0 = a.cn_all[c][0], cn1 = a.cn_all[c][1];
+      const int i = (int)(li % cn0);
+      const int j = (int)((li / cn0) % cn1);
+      const int l = (int)(li / ((long)cn0 * cn1));
+      const int ex = (c & 1) + 2 * i, ey = ((c >> 1) & 1) + 2 * j, ez = (DIM == 3) ? ((c >> 2) & 1) + 2 * l : 0;
+      sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
+    }
+  }
+  __syncthreads();
+
+  // ---- S0: gather nodal values of every slot (velocity, pressure) with
+  //      asynchronous global->shared copies (all loads of the batch in flight);
+  //      prefetch the batch's coefficient-cache block into L2 meanwhile
+  for (int it = threadIdx.x; it < ns * (NC * NQ + NP); it += blockDim.x) {
+    const int s = it / (NC * NQ + NP), r = it % (NC * NQ + NP);
+    if constexpr (MODE == OP_ELM) {
+      // unit vector e_j of the cell's local dofs (velocity c-major, then pressure)
+      const int jcol = (int)((b0 + s) % D::NE);
+      const T v = (r == jcol) ? (T)1 : (T)0;
+      if (r < NC * NQ) sX[s * Cfg::SX + r] = v;
+      else sP[s * NP + (r - NC * NQ)] = v;
+      continue;
+    }
+    const int ci = s / K1, mu = s % K1;
+    const int cell = sCell[ci];
+    const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+    const T* src;
+    T* dst;
+    if (r < NC * NQ) {
+      const int c = r / NQ, q = r % NQ;
+      const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
+      const long g = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz));
+      src = in + (long)mu * a.Mv + c * a.Nq2 + g;
+      dst = sX + s * Cfg::SX + r;
+    } else {
+      const int m = r - NC * NQ;
+      const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
+      const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
+      src = in + (long)K1 * a.Mv + (long)mu * a.Mp + g;
+      dst = sP + s * NP + m;
+    }
+    cp_async_elem<T>(dst, src);
+  }
+  cp_async_commit();
+  if constexpr (MODE == OP_JAC) {
+    const char* cb = reinterpret_cast<const char*>(a.cache) +
+                     (size_t)(a.col_start + b0) * K1 * D::NF_VOL * NQ * sizeof(T);
+    const size_t nbytes = (size_t)ns * D::NF_VOL * NQ * sizeof(T);
+    for (size_t off = (size_t)threadIdx.x * 128; off < nbytes; off += (size_t)blockDim.x * 128)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(cb + off));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---- S1: per (slot, component), in registers: values at the Gauss points
+  //      (Q2 basis, one pass per direction), then the gradient in collocation
+  //      form; per slot: the pressure at the Gauss points (Q1 basis) into sQ
+  constexpr int NPI = (MODE == OP_LIN) ? 0 : 1;  // pressure items per slot
+  for (int it = threadIdx.x; it < ns * (NC + NPI); it += blockDim.x) {
+    if (it >= ns * NC) {
+      const int s = it - ns * NC;
+      T pn[NP], pq[NQ];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) pn[m] = sP[s * NP + m];
+      q1_to_gauss<DIM>(pn, ct.B1, pq);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sQ[s * NQ + q] = pq[q];
+      continue;
+    }
+    const int s = it / NC, c = it % NC;
+    T* xs = sX + s * Cfg::SX + c * NQ;
+    T v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = xs[q];
+    rpass_sym<DIM, 0>(v, ct.BS);
+    rpass_sym<DIM, 1>(v, ct.BS);
+    if constexpr (DIM == 3) rpass_sym<DIM, 2>(v, ct.BS);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) xs[q] = v[q];
+    T* gs = sG + s * Cfg::SG + c * DIM * NQ;
+    rpass_out_d<DIM, 0>(v, sDd[0], gs);
+    rpass_out_d<DIM, 1>(v, sDd[1], gs + NQ);
+    if constexpr (DIM == 3) rpass_out_d<DIM, 2>(v, sDd[2], gs + 2 * NQ);
+  }
+  __syncthreads();
+
+  // ---- S3: pointwise work at every quadrature point of every slot
+  for (int it = threadIdx.x; it < ns * NQ; it += blockDim.x) {
+    const int s = it / NQ, q = it % NQ;
+    const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
+    const long gidx = (MODE == OP_ELM) ? colour_index<DIM>(a, sCell[ci]) : a.col_start + b0 + ci;  // colour-ordered cell index
+    T u[3] = {0, 0, 0}, g[3][3];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      u[c] = sX[s * Cfg::SX + c * NQ + q];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) g[c][j] = sG[s * Cfg::SG + (c * DIM + j) * NQ + q];
+    }
+    const T wq = (DIM == 3) ? ct.WQ3[q] : ct.WQ2[q];
+    if constexpr (MODE == OP_LIN) {
+      // coefficients of the linearisation, FP64 (Sec. 4.1)
+      double A[NS];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) A[i] = (double)g[i][i];
+      A[DIM] = 0.5 * ((double)g[0][1] + (double)g[1][0]);
+      if (DIM == 3) {
+        A[4] = 0.5 * ((double)g[0][2] + (double)g[2][0]);
+        A[5] = 0.5 * ((double)g[1][2] + (double)g[2][1]);
+      }
+      double a2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) a2 += (i < DIM ? 1.0 : 2.0) * A[i] * A[i];
+      const double D2 = a.delta * a.delta + a2;
+      const double mu_m = a.nu * pow(D2, 0.5 * (a.p - 2.0));
+      const double eta = a.nu_inf + mu_m;
+      double cfac = 0.0;
+      if (a.tangent == ST_EXN) {
+        cfac = (a.p - 2.0) * mu_m / D2;
+      } else if (a.tangent == ST_MODN) {
+        const double sig = mu_m * sqrt(a2);
+        const double sc = sig > 0.0 ? fmin(1.0, a.sigma_max / sig) : 0.0;
+        cfac = sc * (a.p - 2.0) * mu_m / D2;
+      }
+      const double tw = (double)wq * a.vol * a.tw[mu];
+      double* cp = a.wcache + ((gidx * K1 + mu) * (long)D::NF_VOL) * NQ + q;
+      cp[0 * NQ] = eta * tw;
+      cp[1 * NQ] = cfac * tw;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) cp[(2 + i) * NQ] = A[i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) cp[(2 + NS + c) * NQ] = -(double)u[c] * tw;
+    } else if constexpr (MODE == OP_JAC || MODE == OP_ELM) {
+      const T* cp = reinterpret_cast<const T*>(a.cache) + ((gidx * K1 + mu) * (long)D::NF_VOL) * NQ + q;
+      const T etaw = cp[0];
+      T nuw[3] = {0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < NC; ++c) nuw[c] = cp[(2 + NS + c) * NQ];
+      const T dpi = sQ[s * NQ + q];  // pressure increment at q (S1)
+      const T tw = wq * (T)(a.vol * a.tw[mu]);
+      const T pd = -dpi * tw;
+      T G[3][3];
+      if constexpr (TAN == 1) {
+        // T(B) = eta B + c (A:B) A with B = D(du); convection -(du (x) u + u (x) du)
+        const T cw = cp[NQ];
+        T Am[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Am[i] = cp[(2 + i) * NQ];
+        T bo[3];  // 2 * off-diagonal entries of D(du)
+        bo[0] = g[0][1] + g[1][0];
+        if (DIM == 3) {
+          bo[1] = g[0][2] + g[2][0];
+          bo[2] = g[1][2] + g[2][1];
+        }
+        T AB = Am[0] * g[0][0] + Am[1] * g[1][1];
+        if (DIM == 3) AB += Am[2] * g[2][2] + Am[3] * bo[0] + Am[4] * bo[1] + Am[5] * bo[2];
+        else AB += Am[2] * bo[0];
+        const T sfac = cw * AB;
+        const T hw = (T)0.5 * etaw;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const T du2 = u[i] + u[i];
+          G[i][i] = etaw * g[i][i] + (sfac * Am[i] + (du2 * nuw[i] + pd));
+        }
+        {
+          const T v01 = hw * bo[0] + (sfac * Am[DIM] + (u[0] * nuw[1] + u[1] * nuw[0]));
+          G[0][1] = v01;
+          G[1][0] = v01;
+        }
+        if (DIM == 3) {
+          const T v02 = hw * bo[1] + (sfac * Am[4] + (u[0] * nuw[2] + u[2] * nuw[0]));
+          const T v12 = hw * bo[2] + (sfac * Am[5] + (u[1] * nuw[2] + u[2] * nuw[1]));
+          G[0][2] = v02;
+          G[2][0] = v02;
+          G[1][2] = v12;
+          G[2][1] = v12;
+        }
+      } else {
+        // Picard: T(B) = eta B, convection -(du (x) u) with the advecting u lagged
+        const T hw = (T)0.5 * etaw;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) {
+            const T bij = (i == j) ? etaw * g[i][i] : hw * (g[i][j] + g[j][i]);
+            G[i][j] = bij + u[i] * nuw[j] + (i == j ? pd : (T)0);
+          }
+      }
+      T div = g[0][0] + g[1][1];
+      if (DIM == 3) div += g[2][2];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = G[c][j];
+      sQ[s * NQ + q] = -div * tw;  // pressure test flux
+    } else {  // OP_RES: F = RHS - LHS, gradient-test flux -(S(Du) - u (x) u - pi I)
+      const T pi = sQ[s * NQ + q];  // pressure at q (S1)
+      T A[3][3];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) A[i][j] = (T)0.5 * (g[i][j] + g[j][i]);
+      T a2 = 0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) a2 += A[i][j] * A[i][j];
+      const T eta = (T)a.nu_inf + (T)a.nu * pow((T)(a.delta * a.delta) + a2, (T)(0.5 * (a.p - 2.0)));
+      const T tw = wq * (T)(a.vol * a.tw[mu]);
+      T div = 0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) div += g[i][i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+          sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = -(eta * A[c][j] - u[c] * u[j] - (c == j ? pi : (T)0)) * tw;
+      sQ[s * NQ + q] = div * tw;
+    }
+  }
+  __syncthreads();
+
+  if constexpr (MODE != OP_LIN) {
+    // ---- S4: per (slot, component), in registers: K_t (x) M_x value term,
+    //      transposed derivative chain, transposed value passes, nodal value
+    //      terms (residual), scatter-add; per (slot, pressure node): pressure test
+    for (int it = threadIdx.x; it < ns * (NC + 1); it += blockDim.x) {
+      if (it < ns * NC) {
+        const int s = it / NC, c = it % NC;
+        const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
+        T acc[NQ];
+        if constexpr (MODE == OP_JAC) {
+          // tv_mu(q) = W(q) sum_j (K_t vol)_{mu j} du_j(q)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            T t = (T)a.KtV[mu * K1] * sX[(ci * K1) * Cfg::SX + c * NQ + q];
+#pragma unroll
+            for (int j = 1; j < K1; ++j) t += (T)a.KtV[mu * K1 + j] * sX[(ci * K1 + j) * Cfg::SX + c * NQ + q];
+            acc[q] = t * ((DIM == 3) ? ct.WQ3[q] : ct.WQ2[q]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) acc[q] = 0;
+        }
+        const T* gs = sG + s * Cfg::SG + c * DIM * NQ;
+        rpass_acc_d<DIM, 0>(acc, sDdt[0], gs);
+        rpass_acc_d<DIM, 1>(acc, sDdt[1], gs + NQ);
+        if constexpr (DIM == 3) rpass_acc_d<DIM, 2>(acc, sDdt[2], gs + 2 * NQ);
+        rpass_sym<DIM, 0>(acc, ct.BtS);
+        rpass_sym<DIM, 1>(acc, ct.BtS);
+        if constexpr (DIM == 3) rpass_sym<DIM, 2>(acc, ct.BtS);
+        const int cell = sCell[ci];
+        const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+        if constexpr (MODE == OP_RES) {
+          // value terms in nodal form: M_e (-sum_j K_ij u_j + m_i v^- + tau w_i f_i)
+          const T* vp = reinterpret_cast<const T*>(a.vprev);
+          const T* ff = reinterpret_cast<const T*>(a.f);
+          T y[NQ];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
+            const long gn = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz)) + c * a.Nq2;
+            T t = vp ? (T)a.mt[mu] * vp[gn] : (T)0;
+#pragma unroll
+            for (int j = 0; j < K1; ++j) t -= (T)a.Kt[mu * K1 + j] * in[(long)j * a.Mv + gn];
+            if (ff) t += (T)a.tw[mu] * ff[(long)mu * a.Mv + gn];
+            y[q] = t;
+          }
+          rpass<DIM, 0>(y, sM1[0]);
+          rpass<DIM, 1>(y, sM1[1]);
+          if constexpr (DIM == 3) rpass<DIM, 2>(y, sM1[2]);
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) acc[q] += y[q];
+        }
+        if constexpr (MODE == OP_ELM) {
+          // column j of the element matrix (rows: velocity c-major, then pressure)
+          const long item = b0 + s;
+          T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) E[(long)(c * NQ + q) * D::NE] = acc[q];
+          continue;
+        }
+        // plain stores into the private buffer of the cell's colour class:
+        // cells of one class share no node, so no two threads write the same
+        // entry; st_node_sum adds the classes' buffers afterwards
+        T* ob = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)mu * a.Mv +
+                c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
+          ob[qx + a.g2[0] * (qy + a.g2[1] * qz)] = acc[q];
+        }
+      } else {
+        // pressure test of the slot, sum-factorised (transposed Q1 passes)
+        const int s = it - ns * NC;
+        const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
+        T fq[NQ], pt[NP];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) fq[q] = sQ[s * NQ + q];
+        gauss_to_q1<DIM>(fq, ct.B1, pt);
+        const int cell = sCell[ci];
+        const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+        if constexpr (MODE == OP_ELM) {
+          const long item = b0 + s;
+          T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
+#pragma unroll
+          for (int m = 0; m < NP; ++m) E[(long)(NC * NQ + m) * D::NE] = pt[m];
+          continue;
+        }
+        T* pb = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
+                (long)mu * a.Mp;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
+          pb[(ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz))] = pt[m];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM, int K1, typename T, int MODE, int TAN>
+__global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpArgs a) {
+  using Cfg = OpCfg<DIM, K1, T>;
+  constexpr int C = Cfg::C, S = Cfg::S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
 
   // balanced chunk of the colour-ordered cells (element-matrix mode: of the items)
   const long ncol = a.ncol;
@@ -395,342 +737,62 @@ __global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT) st_op_kernel(const OpAr
   }
   __syncthreads();
 
-  constexpr int SK = (MODE == OP_ELM) ? 1 : K1;  // slots per batch item
-  constexpr int CB = (MODE == OP_ELM) ? S : C;    // items per batch
-  for (long b0 = cbeg; b0 < cend; b0 += CB) {
-    const int nc = (int)min((long)CB, cend - b0);
-    const int ns = nc * SK;
+  constexpr int CB = (MODE == OP_ELM) ? S : C;  // items per batch
+  for (long b0 = cbeg; b0 < cend; b0 += CB)
+    op_batch<DIM, K1, T, MODE, TAN>(a, b0, (int)min((long)CB, cend - b0), smem_raw, sDd, sDdt, sM1);
+}
 
-    // ---- batch setup: cell ids (element-matrix mode: item = (cell, column))
-    for (int ci = threadIdx.x; ci < nc; ci += blockDim.x) {
-      if constexpr (MODE == OP_ELM) {
-        sCell[ci] = (int)((b0 + ci) / D::NE);
-      } else {
-        // colour-ordered cell index -> colour class c -> cell (o + 2 i, ...)
-        long li = b0 + ci;
-        int c = 0;
-#pragma unroll
-        for (int cc = 1; cc < (1 << DIM); ++cc) c += (li >= a.col_start_all[cc]) ? 1 : 0;
-        li -= a.col_start_all[c];
-        const int cn0 = a.cn_all[c][0], cn1 = a.cn_all[c][1];
-        const int i = (int)(li % cn0);
-        const int j = (int)((li / cn0) % cn1);
-        const int l = (int)(li / ((long)cn0 * cn1));
-        const int ex = (c & 1) + 2 * i, ey = ((c >> 1) & 1) + 2 * j, ez = (DIM == 3) ? ((c >> 2) & 1) + 2 * l : 0;
-        sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
+// Many independent slab problems in one persistent launch: descs[i] is the
+// argument block of instance i (same dim and k, any mesh and parameters);
+// item t of the work queue is cell batch t - first[i] of the instance i with
+// first[i] <= t < first[i+1].  A CTA keeps the block of its current instance
+// in shared memory.
+template <int DIM, int K1, typename T, int MODE, int TAN>
+__global__ void __launch_bounds__(OpCfg<DIM, K1, T>::NT)
+    st_op_kernel_batch(const OpArgs* __restrict__ descs, const long* __restrict__ first, int ninst,
+                       unsigned* __restrict__ queue) {
+  using Cfg = OpCfg<DIM, K1, T>;
+  constexpr int C = Cfg::C;
+  static_assert(MODE != OP_ELM, "element matrices are built per instance");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ OpArgs sA;
+  __shared__ T sDd[3][9], sDdt[3][9], sM1[3][9];
+  __shared__ long sItem;
+  __shared__ int sInst;
+  const long nitems = first[ninst];
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long t = (long)atomicAdd(queue, 1u);
+      int lo = 0, hi = ninst;  // first[lo] <= t < first[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (first[mid] <= t) lo = mid;
+        else hi = mid;
       }
+      sItem = t;
+      sInst = lo;
     }
     __syncthreads();
-
-    // ---- S0: gather nodal values of every slot (velocity, pressure) with
-    //      asynchronous global->shared copies (all loads of the batch in flight);
-    //      prefetch the batch's coefficient-cache block into L2 meanwhile
-    for (int it = threadIdx.x; it < ns * (NC * NQ + NP); it += blockDim.x) {
-      const int s = it / (NC * NQ + NP), r = it % (NC * NQ + NP);
-      if constexpr (MODE == OP_ELM) {
-        // unit vector e_j of the cell's local dofs (velocity c-major, then pressure)
-        const int jcol = (int)((b0 + s) % D::NE);
-        const T v = (r == jcol) ? (T)1 : (T)0;
-        if (r < NC * NQ) sX[s * Cfg::SX + r] = v;
-        else sP[s * NP + (r - NC * NQ)] = v;
-        continue;
+    const long t = sItem;
+    const int i = sInst;
+    if (t >= nitems) break;
+    if (i != cur) {
+      const unsigned* src = reinterpret_cast<const unsigned*>(descs + i);
+      unsigned* dst = reinterpret_cast<unsigned*>(&sA);
+      for (int w = threadIdx.x; w < (int)(sizeof(OpArgs) / sizeof(unsigned)); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x < 27) {
+        const int d = threadIdx.x / 9, e = threadIdx.x % 9;
+        sDd[d][e] = (T)sA.Dd[d][e];
+        sDdt[d][e] = (T)sA.Ddt[d][e];
+        sM1[d][e] = (T)sA.M1d[d][e];
       }
-      const int ci = s / K1, mu = s % K1;
-      const int cell = sCell[ci];
-      const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
-      const T* src;
-      T* dst;
-      if (r < NC * NQ) {
-        const int c = r / NQ, q = r % NQ;
-        const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-        const long g = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz));
-        src = in + (long)mu * a.Mv + c * a.Nq2 + g;
-        dst = sX + s * Cfg::SX + r;
-      } else {
-        const int m = r - NC * NQ;
-        const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
-        const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
-        src = in + (long)K1 * a.Mv + (long)mu * a.Mp + g;
-        dst = sP + s * NP + m;
-      }
-      cp_async_elem<T>(dst, src);
+      __syncthreads();
+      cur = i;
     }
-    cp_async_commit();
-    if constexpr (MODE == OP_JAC) {
-      const char* cb = reinterpret_cast<const char*>(a.cache) +
-                       (size_t)(a.col_start + b0) * K1 * D::NF_VOL * NQ * sizeof(T);
-      const size_t nbytes = (size_t)ns * D::NF_VOL * NQ * sizeof(T);
-      for (size_t off = (size_t)threadIdx.x * 128; off < nbytes; off += (size_t)blockDim.x * 128)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cb + off));
-    }
-    cp_async_wait_all();
-    __syncthreads();
-
-    // ---- S1: per (slot, component), in registers: values at the Gauss points
-    //      (Q2 basis, one pass per direction), then the gradient in collocation
-    //      form; per slot: the pressure at the Gauss points (Q1 basis) into sQ
-    constexpr int NPI = (MODE == OP_LIN) ? 0 : 1;  // pressure items per slot
-    for (int it = threadIdx.x; it < ns * (NC + NPI); it += blockDim.x) {
-      if (it >= ns * NC) {
-        const int s = it - ns * NC;
-        T pn[NP], pq[NQ];
-#pragma unroll
-        for (int m = 0; m < NP; ++m) pn[m] = sP[s * NP + m];
-        q1_to_gauss<DIM>(pn, ct.B1, pq);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) sQ[s * NQ + q] = pq[q];
-        continue;
-      }
-      const int s = it / NC, c = it % NC;
-      T* xs = sX + s * Cfg::SX + c * NQ;
-      T v[NQ];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] = xs[q];
-      rpass_sym<DIM, 0>(v, ct.BS);
-      rpass_sym<DIM, 1>(v, ct.BS);
-      if constexpr (DIM == 3) rpass_sym<DIM, 2>(v, ct.BS);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) xs[q] = v[q];
-      T* gs = sG + s * Cfg::SG + c * DIM * NQ;
-      rpass_out_d<DIM, 0>(v, sDd[0], gs);
-      rpass_out_d<DIM, 1>(v, sDd[1], gs + NQ);
-      if constexpr (DIM == 3) rpass_out_d<DIM, 2>(v, sDd[2], gs + 2 * NQ);
-    }
-    __syncthreads();
-
-    // ---- S3: pointwise work at every quadrature point of every slot
-    for (int it = threadIdx.x; it < ns * NQ; it += blockDim.x) {
-      const int s = it / NQ, q = it % NQ;
-      const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
-      const long gidx = (MODE == OP_ELM) ? colour_index<DIM>(a, sCell[ci]) : a.col_start + b0 + ci;  // colour-ordered cell index
-      T u[3] = {0, 0, 0}, g[3][3];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        u[c] = sX[s * Cfg::SX + c * NQ + q];
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) g[c][j] = sG[s * Cfg::SG + (c * DIM + j) * NQ + q];
-      }
-      const T wq = (DIM == 3) ? ct.WQ3[q] : ct.WQ2[q];
-      if constexpr (MODE == OP_LIN) {
-        // coefficients of the linearisation, FP64 (Sec. 4.1)
-        double A[NS];
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) A[i] = (double)g[i][i];
-        A[DIM] = 0.5 * ((double)g[0][1] + (double)g[1][0]);
-        if (DIM == 3) {
-          A[4] = 0.5 * ((double)g[0][2] + (double)g[2][0]);
-          A[5] = 0.5 * ((double)g[1][2] + (double)g[2][1]);
-        }
-        double a2 = 0.0;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) a2 += (i < DIM ? 1.0 : 2.0) * A[i] * A[i];
-        const double D2 = a.delta * a.delta + a2;
-        const double mu_m = a.nu * pow(D2, 0.5 * (a.p - 2.0));
-        const double eta = a.nu_inf + mu_m;
-        double cfac = 0.0;
-        if (a.tangent == ST_EXN) {
-          cfac = (a.p - 2.0) * mu_m / D2;
-        } else if (a.tangent == ST_MODN) {
-          const double sig = mu_m * sqrt(a2);
-          const double sc = sig > 0.0 ? fmin(1.0, a.sigma_max / sig) : 0.0;
-          cfac = sc * (a.p - 2.0) * mu_m / D2;
-        }
-        const double tw = (double)wq * a.vol * a.tw[mu];
-        double* cp = a.wcache + ((gidx * K1 + mu) * (long)D::NF_VOL) * NQ + q;
-        cp[0 * NQ] = eta * tw;
-        cp[1 * NQ] = cfac * tw;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) cp[(2 + i) * NQ] = A[i];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) cp[(2 + NS + c) * NQ] = -(double)u[c] * tw;
-      } else if constexpr (MODE == OP_JAC || MODE == OP_ELM) {
-        const T* cp = reinterpret_cast<const T*>(a.cache) + ((gidx * K1 + mu) * (long)D::NF_VOL) * NQ + q;
-        const T etaw = cp[0];
-        T nuw[3] = {0, 0, 0};
-#pragma unroll
-        for (int c = 0; c < NC; ++c) nuw[c] = cp[(2 + NS + c) * NQ];
-        const T dpi = sQ[s * NQ + q];  // pressure increment at q (S1)
-        const T tw = wq * (T)(a.vol * a.tw[mu]);
-        const T pd = -dpi * tw;
-        T G[3][3];
-        if constexpr (TAN == 1) {
-          // T(B) = eta B + c (A:B) A with B = D(du); convection -(du (x) u + u (x) du)
-          const T cw = cp[NQ];
-          T Am[NS];
-#pragma unroll
-          for (int i = 0; i < NS; ++i) Am[i] = cp[(2 + i) * NQ];
-          T bo[3];  // 2 * off-diagonal entries of D(du)
-          bo[0] = g[0][1] + g[1][0];
-          if (DIM == 3) {
-            bo[1] = g[0][2] + g[2][0];
-            bo[2] = g[1][2] + g[2][1];
-          }
-          T AB = Am[0] * g[0][0] + Am[1] * g[1][1];
-          if (DIM == 3) AB += Am[2] * g[2][2] + Am[3] * bo[0] + Am[4] * bo[1] + Am[5] * bo[2];
-          else AB += Am[2] * bo[0];
-          const T sfac = cw * AB;
-          const T hw = (T)0.5 * etaw;
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) {
-            const T du2 = u[i] + u[i];
-            G[i][i] = etaw * g[i][i] + (sfac * Am[i] + (du2 * nuw[i] + pd));
-          }
-          {
-            const T v01 = hw * bo[0] + (sfac * Am[DIM] + (u[0] * nuw[1] + u[1] * nuw[0]));
-            G[0][1] = v01;
-            G[1][0] = v01;
-          }
-          if (DIM == 3) {
-            const T v02 = hw * bo[1] + (sfac * Am[4] + (u[0] * nuw[2] + u[2] * nuw[0]));
-            const T v12 = hw * bo[2] + (sfac * Am[5] + (u[1] * nuw[2] + u[2] * nuw[1]));
-            G[0][2] = v02;
-            G[2][0] = v02;
-            G[1][2] = v12;
-            G[2][1] = v12;
-          }
-        } else {
-          // Picard: T(B) = eta B, convection -(du (x) u) with the advecting u lagged
-          const T hw = (T)0.5 * etaw;
-#pragma unroll
-          for (int i = 0; i < DIM; ++i)
-#pragma unroll
-            for (int j = 0; j < DIM; ++j) {
-              const T bij = (i == j) ? etaw * g[i][i] : hw * (g[i][j] + g[j][i]);
-              G[i][j] = bij + u[i] * nuw[j] + (i == j ? pd : (T)0);
-            }
-        }
-        T div = g[0][0] + g[1][1];
-        if (DIM == 3) div += g[2][2];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int j = 0; j < DIM; ++j) sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = G[c][j];
-        sQ[s * NQ + q] = -div * tw;  // pressure test flux
-      } else {  // OP_RES: F = RHS - LHS, gradient-test flux -(S(Du) - u (x) u - pi I)
-        const T pi = sQ[s * NQ + q];  // pressure at q (S1)
-        T A[3][3];
-#pragma unroll
-        for (int i = 0; i < DIM; ++i)
-#pragma unroll
-          for (int j = 0; j < DIM; ++j) A[i][j] = (T)0.5 * (g[i][j] + g[j][i]);
-        T a2 = 0;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i)
-#pragma unroll
-          for (int j = 0; j < DIM; ++j) a2 += A[i][j] * A[i][j];
-        const T eta = (T)a.nu_inf + (T)a.nu * pow((T)(a.delta * a.delta) + a2, (T)(0.5 * (a.p - 2.0)));
-        const T tw = wq * (T)(a.vol * a.tw[mu]);
-        T div = 0;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) div += g[i][i];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-          for (int j = 0; j < DIM; ++j)
-            sG[s * Cfg::SG + (c * DIM + j) * NQ + q] = -(eta * A[c][j] - u[c] * u[j] - (c == j ? pi : (T)0)) * tw;
-        sQ[s * NQ + q] = div * tw;
-      }
-    }
-    __syncthreads();
-
-    if constexpr (MODE != OP_LIN) {
-      // ---- S4: per (slot, component), in registers: K_t (x) M_x value term,
-      //      transposed derivative chain, transposed value passes, nodal value
-      //      terms (residual), scatter-add; per (slot, pressure node): pressure test
-      for (int it = threadIdx.x; it < ns * (NC + 1); it += blockDim.x) {
-        if (it < ns * NC) {
-          const int s = it / NC, c = it % NC;
-          const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
-          T acc[NQ];
-          if constexpr (MODE == OP_JAC) {
-            // tv_mu(q) = W(q) sum_j (K_t vol)_{mu j} du_j(q)
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-              T t = (T)a.KtV[mu * K1] * sX[(ci * K1) * Cfg::SX + c * NQ + q];
-#pragma unroll
-              for (int j = 1; j < K1; ++j) t += (T)a.KtV[mu * K1 + j] * sX[(ci * K1 + j) * Cfg::SX + c * NQ + q];
-              acc[q] = t * ((DIM == 3) ? ct.WQ3[q] : ct.WQ2[q]);
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) acc[q] = 0;
-          }
-          const T* gs = sG + s * Cfg::SG + c * DIM * NQ;
-          rpass_acc_d<DIM, 0>(acc, sDdt[0], gs);
-          rpass_acc_d<DIM, 1>(acc, sDdt[1], gs + NQ);
-          if constexpr (DIM == 3) rpass_acc_d<DIM, 2>(acc, sDdt[2], gs + 2 * NQ);
-          rpass_sym<DIM, 0>(acc, ct.BtS);
-          rpass_sym<DIM, 1>(acc, ct.BtS);
-          if constexpr (DIM == 3) rpass_sym<DIM, 2>(acc, ct.BtS);
-          const int cell = sCell[ci];
-          const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
-          if constexpr (MODE == OP_RES) {
-            // value terms in nodal form: M_e (-sum_j K_ij u_j + m_i v^- + tau w_i f_i)
-            const T* vp = reinterpret_cast<const T*>(a.vprev);
-            const T* ff = reinterpret_cast<const T*>(a.f);
-            T y[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-              const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-              const long gn = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz)) + c * a.Nq2;
-              T t = vp ? (T)a.mt[mu] * vp[gn] : (T)0;
-#pragma unroll
-              for (int j = 0; j < K1; ++j) t -= (T)a.Kt[mu * K1 + j] * in[(long)j * a.Mv + gn];
-              if (ff) t += (T)a.tw[mu] * ff[(long)mu * a.Mv + gn];
-              y[q] = t;
-            }
-            rpass<DIM, 0>(y, sM1[0]);
-            rpass<DIM, 1>(y, sM1[1]);
-            if constexpr (DIM == 3) rpass<DIM, 2>(y, sM1[2]);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) acc[q] += y[q];
-          }
-          if constexpr (MODE == OP_ELM) {
-            // column j of the element matrix (rows: velocity c-major, then pressure)
-            const long item = b0 + s;
-            T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) E[(long)(c * NQ + q) * D::NE] = acc[q];
-            continue;
-          }
-          // plain stores into the private buffer of the cell's colour class:
-          // cells of one class share no node, so no two threads write the same
-          // entry; st_node_sum adds the classes' buffers afterwards
-          T* ob = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)mu * a.Mv +
-                  c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) {
-            const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-            ob[qx + a.g2[0] * (qy + a.g2[1] * qz)] = acc[q];
-          }
-        } else {
-          // pressure test of the slot, sum-factorised (transposed Q1 passes)
-          const int s = it - ns * NC;
-          const int ci = s / SK, mu = (MODE == OP_ELM) ? a.elm_mu : s % SK;
-          T fq[NQ], pt[NP];
-#pragma unroll
-          for (int q = 0; q < NQ; ++q) fq[q] = sQ[s * NQ + q];
-          gauss_to_q1<DIM>(fq, ct.B1, pt);
-          const int cell = sCell[ci];
-          const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
-          if constexpr (MODE == OP_ELM) {
-            const long item = b0 + s;
-            T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
-#pragma unroll
-            for (int m = 0; m < NP; ++m) E[(long)(NC * NQ + m) * D::NE] = pt[m];
-            continue;
-          }
-          T* pb = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
-                  (long)mu * a.Mp;
-#pragma unroll
-          for (int m = 0; m < NP; ++m) {
-            const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
-            pb[(ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz))] = pt[m];
-          }
-        }
-      }
-    }
-    __syncthreads();
+    const long b0 = (t - first[i]) * C;
+    op_batch<DIM, K1, T, MODE, TAN>(sA, b0, (int)min((long)C, sA.ncol - b0), smem_raw, sDd, sDdt, sM1);
   }
 }
 

@@ -45,3 +45,18 @@ def test_setup_rejects_bad_parameters_without_gpu():
         assert lib.st_setup_mesh(ctypes.byref(P), None, ctypes.byref(h)) == st.ST_EINVAL
     assert lib.st_setup_mesh(None, None, ctypes.byref(h)) == st.ST_EINVAL
     assert lib.st_destroy(None) == st.ST_OK
+
+
+def test_batch_setup_rejects_mixed_dim_or_k_without_gpu():
+    # dim / k must agree across a batch; checked before any CUDA call
+    import paper_2603_28706_gb300 as st
+    import st_inputs as si
+    lib = st.load()
+    b = ctypes.c_void_p()
+    for other in (dict(k=2), dict(dim=2, nx=4, ny=4)):
+        arr = (st.StParams * 2)(st.params(si.base_params(k=1)), st.params(si.base_params(**other)))
+        assert lib.st_batch_setup(arr, 2, None, ctypes.byref(b)) == st.ST_EINVAL
+    assert lib.st_batch_setup(None, 1, None, ctypes.byref(b)) == st.ST_EINVAL
+    arr = (st.StParams * 1)(st.params(si.base_params()))
+    assert lib.st_batch_setup(arr, 0, None, ctypes.byref(b)) == st.ST_EINVAL
+    assert lib.st_batch_destroy(None) == st.ST_OK

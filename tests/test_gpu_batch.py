@@ -1,0 +1,110 @@
+"""Batched slab problems (st_batch_*): instances of different meshes and
+(p, delta) in one persistent volume launch must give the same vectors as the
+single-problem calls (the same kernels per cell: bitwise), and the oracle's
+within the operator tolerances; the concurrent Newton steps must reproduce
+the single-problem Newton steps."""
+import numpy as np
+import pytest
+
+import oracle
+import st_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gpu():
+    import paper_2603_28706_gb300 as st
+    return st
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def instances(dim):
+    if dim == 3:
+        return [si.base_params(dim=3, nx=4, ny=4, nz=4, k=1, p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05),
+                si.base_params(dim=3, nx=6, ny=3, nz=2, k=1, p=1.25, delta=1e-3, nu=1e-3, nu_inf=1e-4,
+                               sigma_max=1e-3, inflow_profile=1),
+                si.base_params(dim=3, nx=3, ny=5, nz=3, k=1, p=1.8, delta=1e-2, nu=0.5, nu_inf=1e-3, sigma_max=0.3)]
+    return [si.base_params(dim=2, nx=8, ny=8, k=2, p=1.5, delta=1e-2, nu=1.0, nu_inf=1e-3, sigma_max=1.0),
+            si.base_params(dim=2, nx=5, ny=7, k=2, p=1.2, delta=1e-4, nu=1e-3, nu_inf=1e-4, sigma_max=1e-3,
+                           inflow_profile=1)]
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_batch_operator_matches_single_and_oracle(dim):
+    st = gpu()
+    plist = instances(dim)
+    U = [si.uniform_state(p, 10 + i) for i, p in enumerate(plist)]
+    dU = [si.uniform_state(p, 20 + i) for i, p in enumerate(plist)]
+    vp = [si.uniform(oracle.sizes(p)["Mv"], 30 + i) for i, p in enumerate(plist)]
+    b = st.Batch(plist)
+    singles = [st.Problem(p) for p in plist]
+    for prec, dt in ((st.ST_FP64, torch.float64), (st.ST_FP32, torch.float32)):
+        Rb = b.residual([dev(u, dt) for u in U], [dev(v, dt) for v in vp], prec=prec)
+        for i, p in enumerate(plist):
+            Rs = singles[i].residual(dev(U[i], dt), dev(vp[i], dt), prec=prec)
+            assert torch.equal(Rb[i], Rs), ("residual", prec, i)
+    for tg, to in ((2, oracle.MODN), (1, oracle.EXN), (0, oracle.PIC)):
+        b.linearize(tg, [dev(u) for u in U])
+        for prec, dt in ((st.ST_FP64, torch.float64), (st.ST_FP32, torch.float32)):
+            Jb = b.jacobian_apply(tg, [dev(x, dt) for x in dU], prec=prec)
+            for i, p in enumerate(plist):
+                singles[i].linearize(tg, dev(U[i]))
+                Js = singles[i].jacobian_apply(tg, dev(dU[i], dt), prec=prec)
+                assert torch.equal(Jb[i], Js), ("jacobian", tg, prec, i)
+        # one instance against the oracle
+        Jr = oracle.jacobian_apply(plist[1], to, U[1], dU[1])
+        Jb = b.jacobian_apply(tg, [dev(x) for x in dU])
+        err = np.abs(Jb[1].cpu().numpy() - Jr).max() / np.abs(Jr).max()
+        assert err <= 1e-12, (tg, err)
+    for s in singles:
+        s.close()
+    b.close()
+
+
+def test_batch_jacobian_needs_linearisation():
+    st = gpu()
+    plist = instances(3)[:2]
+    b = st.Batch(plist)
+    dU = [dev(si.uniform_state(p, 1)) for p in plist]
+    with pytest.raises(st.StError):
+        b.jacobian_apply(2, dU)
+    b.linearize(1, [dev(si.uniform_state(p, 2)) for p in plist])
+    with pytest.raises(st.StError):
+        b.jacobian_apply(2, dU)  # linearised with exN, applied with modN
+    b.close()
+
+
+def test_batch_newton_matches_single():
+    st = gpu()
+    plist = [si.base_params(dim=3, nx=4, ny=4, nz=4, k=1, dt=0.05, p=1.4, delta=0.1, nu=0.1, nu_inf=0.01,
+                            sigma_max=0.02, levels=2, inflow_profile=1, tol_rel=1e-10, tol_abs=1e-14,
+                            coarse_sweeps=4, newton_maxit=40),
+             si.base_params(dim=3, nx=4, ny=2, nz=2, k=1, dt=0.05, p=1.6, delta=0.05, nu=0.1, nu_inf=0.01,
+                            sigma_max=0.02, levels=2, tol_rel=1e-10, tol_abs=1e-14, coarse_sweeps=4,
+                            newton_maxit=40),
+             si.base_params(dim=3, nx=2, ny=2, nz=2, k=1, dt=0.05, p=1.3, delta=0.1, nu=0.1, nu_inf=0.01,
+                            sigma_max=0.02, levels=1, tol_rel=1e-10, tol_abs=1e-14, coarse_sweeps=4,
+                            newton_maxit=40)]
+    starts = []
+    for i, p in enumerate(plist):
+        s = oracle.sizes(p)
+        vprev = 0.3 * si.fourier_velocity(p, 3 + i)[0].reshape(-1)
+        starts.append((np.concatenate([vprev] * (p["k"] + 1) + [np.zeros((p["k"] + 1) * s["Mp"])]), vprev))
+    b = st.Batch(plist)
+    for prec in (st.ST_FP64, st.ST_FP32):
+        Ub = [dev(u) for u, _ in starts]
+        status, infos = b.newton_step(2, Ub, [dev(v) for _, v in starts], vcycle_prec=prec)
+        assert status == st.ST_OK
+        for i, p in enumerate(plist):
+            prob = st.Problem(p)
+            Us = dev(starts[i][0])
+            s1, info1 = prob.newton_step(2, Us, dev(starts[i][1]), vcycle_prec=prec)
+            assert s1 == st.ST_OK
+            assert infos[i]["newton_iters"] == info1["newton_iters"]
+            assert torch.equal(Ub[i], Us), (prec, i, (Ub[i] - Us).abs().max().item())
+            prob.close()
+    b.close()
