@@ -424,6 +424,9 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_face, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_cap0, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_cap1, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, 16 * sizeof(int), h->stream);
   if (e != cudaSuccess) {
     st_destroy(h);
@@ -460,6 +463,9 @@ st_status st_destroy(st_problem* h) {
   if (h->s_face) cudaStreamDestroy(h->s_face);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->s_cap) cudaStreamDestroy(h->s_cap);
+  if (h->ev_cap0) cudaEventDestroy(h->ev_cap0);
+  if (h->ev_cap1) cudaEventDestroy(h->ev_cap1);
   delete h;
   return ST_OK;
 }

@@ -154,6 +154,8 @@ struct st_problem {
   void* d_cbuf32 = nullptr;        // the same in FP32 (entries no cell of a class touches stay zero)
   cudaStream_t s_face = nullptr;   // internal stream: face kernels overlap the volume kernels
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t s_cap = nullptr;    // internal stream of the V-cycle (captured as a graph)
+  cudaEvent_t ev_cap0 = nullptr, ev_cap1 = nullptr;
   std::string last_error;
   bool precond_valid = false;
   int precond_prec = -1;

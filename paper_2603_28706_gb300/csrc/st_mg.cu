@@ -795,13 +795,30 @@ struct MgState {
   int nbc = 0;
   double* d_tab = nullptr;       // 1D transfer tables on the device (P2, P1)
   double* d_pch = nullptr;       // child <- parent local prolongation matrices [2^d][NE][NE]
+  // the V-cycle as a CUDA graph, for the (r, d, precision, tangent) it was captured with
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_r = nullptr;
+  void* g_d = nullptr;
+  int g_prec = -1, g_tangent = -1;
+  bool g_seen = false;           // the key was run once eagerly (all lazy initialisation done)
+  bool g_failed = false;         // capture failed for this key: eager
 };
 
 namespace {
 
 size_t esz(int prec) { return prec == ST_FP64 ? sizeof(double) : sizeof(float); }
 
+void drop_graph(MgState* m) {
+  if (m->gexec) cudaGraphExecDestroy(m->gexec);
+  m->gexec = nullptr;
+  m->g_seen = false;
+  m->g_failed = false;
+  m->g_r = nullptr;
+  m->g_d = nullptr;
+}
+
 void free_mg(MgState* m) {
+  drop_graph(m);
   for (auto& l : m->L) {
     cudaFree(l.E);
     cudaFree(l.LU);
@@ -1197,11 +1214,63 @@ st_status mg_vanka(st_problem* h, int level, int sweeps, st_prec prec, const voi
   return cuda_check(h, e, "st_vanka_smooth");
 }
 
+// One V-cycle.  The launch sequence depends only on the buffers, the
+// precision and the tangent (the hierarchy's contents change between calls,
+// its storage does not), so it is captured once as a CUDA graph and replayed:
+// the first call with a new (r, d, precision, tangent) runs eagerly, the
+// second captures, later ones launch the graph.
+// The V-cycle runs on the problem's internal capture stream (the caller's
+// stream may be the legacy default stream, which cannot be captured),
+// ordered after and before the caller's stream by events.
+cudaError_t vcycle_on_cap(st_problem* h, MgState* m, st_prec prec, const void* r, void* d) {
+  const int L = (int)h->lev.size() - 1;
+  auto run = [&]() {
+    return prec == ST_FP64 ? vcycle_rec<double>(h, m, L, (const double*)r, (double*)d)
+                           : vcycle_rec<float>(h, m, L, (const float*)r, (float*)d);
+  };
+  const bool same = m->g_seen && m->g_r == r && m->g_d == d && m->g_prec == (int)prec &&
+                    m->g_tangent == h->lin_tangent;
+  if (same && m->gexec) return cudaGraphLaunch(m->gexec, h->stream);
+  if (!same || m->g_failed) {
+    if (!same) {
+      drop_graph(m);
+      m->g_r = r;
+      m->g_d = d;
+      m->g_prec = (int)prec;
+      m->g_tangent = h->lin_tangent;
+      m->g_seen = true;
+    }
+    return run();
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t er = run();
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (er != cudaSuccess) e = er;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {  // capture unavailable: stay eager for this key
+    m->gexec = nullptr;
+    m->g_failed = true;
+    cudaGetLastError();
+    return run();
+  }
+  return cudaGraphLaunch(m->gexec, h->stream);
+}
+
 st_status mg_vcycle(st_problem* h, st_prec prec, const void* r, void* d) {
   MgState* m = (MgState*)h->mg;
-  const int L = (int)h->lev.size() - 1;
-  cudaError_t e = prec == ST_FP64 ? vcycle_rec<double>(h, m, L, (const double*)r, (double*)d)
-                                  : vcycle_rec<float>(h, m, L, (const float*)r, (float*)d);
+  cudaStream_t user = h->stream;
+  cudaError_t e = cudaEventRecord(h->ev_cap0, user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_cap, h->ev_cap0, 0);
+  if (e != cudaSuccess) return cuda_check(h, e, "st_vcycle");
+  h->stream = h->s_cap;
+  e = vcycle_on_cap(h, m, prec, r, d);
+  h->stream = user;
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_cap1, h->s_cap);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, h->ev_cap1, 0);
   return cuda_check(h, e, "st_vcycle");
 }
 

@@ -39,6 +39,8 @@ struct KrylovWs {
   double* dU = nullptr;
   float* r32 = nullptr;
   float* d32 = nullptr;
+  double* vr64 = nullptr;   // FP64 V-cycle input / output (fixed buffers)
+  double* vd64 = nullptr;
   double* dots = nullptr;   // 2(m+1) + 2
   double* part = nullptr;   // 128 (m+1)
   double* coef = nullptr;   // m + 1
@@ -57,6 +59,8 @@ void free_ws(KrylovWs* k) {
   cudaFree(k->Rt);
   cudaFree(k->dU);
   cudaFree(k->r32);
+  cudaFree(k->vr64);
+  cudaFree(k->vd64);
   cudaFree(k->d32);
   cudaFree(k->dots);
   cudaFree(k->part);
@@ -78,6 +82,8 @@ cudaError_t get_ws(st_problem* h, KrylovWs*& k) {
     if (e == cudaSuccess) e = cudaMalloc(p, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&k->mwork, 2 * n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&k->r32, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&k->vr64, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&k->vd64, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&k->d32, n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&k->dots, (2 * (m + 1) + 2) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&k->part, 128 * (size_t)(m + 1) * sizeof(double));
@@ -109,7 +115,15 @@ cudaError_t japply(st_problem* h, const double* x, double* y) {
 }
 
 st_status precond(st_problem* h, KrylovWs* k, st_prec prec, const double* v, double* z) {
-  if (prec == ST_FP64) return mg_vcycle(h, ST_FP64, v, z);
+  // the V-cycle runs on fixed buffers (so that its captured graph is reused)
+  if (prec == ST_FP64) {
+    cudaError_t e = cudaMemcpyAsync(k->vr64, v, k->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "fgmres copy");
+    st_status s = mg_vcycle(h, ST_FP64, k->vr64, k->vd64);
+    if (s != ST_OK) return s;
+    return cuda_check(h, cudaMemcpyAsync(z, k->vd64, k->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream),
+                      "fgmres copy");
+  }
   cudaError_t e = cast_f64_f32(v, k->r32, k->n, h->stream);
   if (e != cudaSuccess) return cuda_check(h, e, "fgmres cast");
   st_status s = mg_vcycle(h, ST_FP32, k->r32, k->d32);
