@@ -135,6 +135,96 @@ def newton_comparison(st, torch, mesh=(128, 32, 32), arms=("mixed", "fp64")):
     return out
 
 
+BATCH_WORKLOAD = ("64 independent 3D unit-cube instances, n^3 hexes with n drawn from {8, 10, .., 32}, Q2/Q1, "
+                  "dG(1), p ~ U[1.1, 1.9], delta = 10^U[-6, -2], nu=1e-3, nu_inf=1e-4, smooth random velocity "
+                  "(8 Fourier modes, seed i); FP64 modN Jacobian apply of all instances in one persistent launch")
+BATCH_NEWTON_WORKLOAD = ("8 channel instances 4x1x1 from rest, 4n x n x n hexes with n in {4, 6, 8}, dG(1), p ~ U[1.5, 1.9], "
+                         "delta = 10^U[-3, -2]; one modN Newton step each to |R|_M <= 1e-8 |R0|_M, FP32 V-cycle "
+                         "(2 levels); concurrent (one thread and stream each) vs one after another")
+
+
+def batched_comparison(st, torch):
+    """Throughput of the batched operator (st_batch_jacobian_apply: one
+    persistent volume launch over all instances) against the same applies
+    issued instance by instance, and the concurrent batched Newton step
+    against sequential single Newton steps."""
+    rng = np.random.default_rng(0)
+    plist = []
+    for i in range(64):
+        n = 2 * int(rng.integers(4, 17))
+        plist.append(si.base_params(dim=3, nx=n, ny=n, nz=n, k=1, dt=0.01, p=float(rng.uniform(1.1, 1.9)),
+                                    delta=float(10 ** rng.uniform(-6, -2)), nu=1e-3, nu_inf=1e-4, sigma_max=1e-3))
+    b = st.Batch(plist)
+    U = [torch.from_numpy(si.fourier_state(p, i)).cuda() for i, p in enumerate(plist)]
+    dU = [torch.from_numpy(si.uniform_state(p, 100 + i)).cuda() for i, p in enumerate(plist)]
+    out_b = [torch.empty_like(x) for x in dU]
+    ndofs = sum(b.num_dofs(i) for i in range(len(plist)))
+    b.linearize(st.ST_MODN, U)
+    singles = [st.Problem(p) for p in plist]
+    out_s = [torch.empty_like(x) for x in dU]
+    for i, sp in enumerate(singles):
+        sp.linearize(st.ST_MODN, U[i])
+    reps = 10
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    tb = timed(lambda: b.jacobian_apply(st.ST_MODN, dU, out_b))
+    ts = timed(lambda: [sp.jacobian_apply(st.ST_MODN, dU[i], out=out_s[i]) for i, sp in enumerate(singles)])
+    same = all(torch.equal(out_b[i], out_s[i]) for i in range(len(plist)))
+    for sp in singles:
+        sp.close()
+    b.close()
+    del U, dU, out_b, out_s
+    torch.cuda.empty_cache()
+    res = {"workload": BATCH_WORKLOAD, "instances": len(plist), "dofs": ndofs, "batched_ms": tb,
+           "one_by_one_ms": ts, "batched_dofs_per_s": ndofs / (tb * 1e-3),
+           "one_by_one_dofs_per_s": ndofs / (ts * 1e-3), "bitwise_equal": same}
+    # Newton: concurrent instances vs one after another
+    nl = []
+    for i in range(8):
+        nx = 8 * int(rng.integers(2, 5))
+        nl.append(si.config(5, nx=nx, ny=nx // 4, nz=nx // 4, levels=2, p=float(rng.uniform(1.5, 1.9)),
+                            delta=float(10 ** rng.uniform(-3, -2)), tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=4,
+                            newton_maxit=30))
+    b = st.Batch(nl)
+    n_i = [b.num_dofs(i) for i in range(len(nl))]
+    v_i = [b.velocity_size(i) for i in range(len(nl))]
+    Ub = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in n_i]
+    vp = [torch.zeros(v, dtype=torch.float64, device="cuda") for v in v_i]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status_b, infos = b.newton_step(st.ST_MODN, Ub, vp, vcycle_prec=st.ST_FP32, raise_on_fail=False)
+    torch.cuda.synchronize()
+    tcb = time.perf_counter() - t0
+    b.close()
+    tseq, ok_seq = 0.0, True
+    for i, p in enumerate(nl):
+        sp = st.Problem(p)
+        Us = torch.zeros(n_i[i], dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s1, _ = sp.newton_step(st.ST_MODN, Us, vp[i], vcycle_prec=st.ST_FP32, raise_on_fail=False)
+        torch.cuda.synchronize()
+        tseq += time.perf_counter() - t0
+        ok_seq = ok_seq and s1 == st.ST_OK and torch.equal(Us, Ub[i])
+        sp.close()
+    res["newton"] = {"workload": BATCH_NEWTON_WORKLOAD, "concurrent_s": tcb, "one_by_one_s": tseq,
+                     "status": int(status_b), "newton_iters": [x["newton_iters"] for x in infos],
+                     "same_result_as_single": bool(ok_seq)}
+    return res
+
+
 class ClockSampler:
     def __init__(self, index):
         self.index = index
@@ -241,6 +331,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the mixed vs FP64 Newton-step comparison")
     ap.add_argument("--newton-only", action="store_true", help="run only the Newton-step comparison and print it")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-instance comparison")
+    ap.add_argument("--batched-only", action="store_true", help="run only the batched-instance comparison")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     args = ap.parse_args()
@@ -259,6 +351,9 @@ def main():
     st.build.build()
     if args.newton_only:
         print(json.dumps(newton_comparison(st, torch, tuple(args.newton_mesh), tuple(args.newton_arms.split(",")))))
+        return
+    if args.batched_only:
+        print(json.dumps(batched_comparison(st, torch)))
         return
     stream = torch.cuda.current_stream()
     prob = st.Problem(p, stream=stream)
@@ -348,6 +443,7 @@ def main():
            "h2d_bytes_per_step": len(tangents) * 2 * 8 * n, "d2h_bytes_per_step": len(tangents) * 8 * n}
 
     newton = None if (args.no_newton or rank != 0) else newton_comparison(st, torch, tuple(args.newton_mesh))
+    batched = None if (args.no_batched or rank != 0) else batched_comparison(st, torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -370,7 +466,7 @@ def main():
                                  (8 * 2 * 32768 * 27 * 11 / 1e6),
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
-                "newton": newton,
+                "newton": newton, "batched": batched,
                 "clocks": clk.summary()}
         print(json.dumps(line))
     prob.close()

@@ -171,6 +171,101 @@ __global__ void galerkin_kernel(const T* __restrict__ Ef, T* __restrict__ Ec, in
   }
 }
 
+// Sum-factorised Galerkin coarsening.  The child prolongation is block
+// diagonal with Kronecker blocks: per velocity component P2[oz] (x) P2[oy]
+// (x) P2[ox] (3x3 1D blocks, rows child node, columns parent node), for the
+// pressure P1[oz] (x) P1[oy] (x) P1[ox] (2x2), o the child's offset.  So
+// T = E_f P applies P^T to every row segment and R += P^T T to every column
+// segment, one 1D pass per direction (3^d x 3 instead of 3^d x 3^d FMA per
+// segment).  One CTA per (coarse cell, node); E_f, T, R in shared memory.
+template <int DIM, int N1, typename T>
+__device__ __forceinline__ void kron_pass_t(T* v, const T (*m)[3][3], const int* off) {
+  // v (N1^DIM, x fastest) <- (M_z (x) M_y (x) M_x)^T v, M_d = m[off[d]] (N1 x N1 used)
+  constexpr int NT = DIM == 3 ? N1 * N1 * N1 : N1 * N1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? N1 : N1 * N1);
+    const T(*M)[3] = m[off[d]];
+    T u[NT];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+      const int ci = (i / st) % N1;  // output (parent) index along d
+      const int base = i - ci * st;
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) acc = fma(M[j][ci], v[base + j * st], acc);
+      u[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < NT; ++i) v[i] = u[i];
+  }
+}
+
+// one segment of E (row r or column b) through P_seg^T; ld: stride between segment entries
+template <int DIM, int N1, typename T, bool ACC>
+__device__ __forceinline__ void galerkin_segment(const T* src, T* dst, int ld, const T (*m)[3][3], const int* off) {
+  constexpr int NT = DIM == 3 ? N1 * N1 * N1 : N1 * N1;
+  T v[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) v[j] = src[j * ld];
+  kron_pass_t<DIM, N1, T>(v, m, off);
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (ACC) dst[j * ld] += v[j];
+    else dst[j * ld] = v[j];
+  }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) galerkin_sf_kernel(const T* __restrict__ Ef, T* __restrict__ Ec, int ncx,
+                                                          int ncy, int ncz, int K1, const double* __restrict__ tab) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sE = reinterpret_cast<T*>(smraw);  // child matrix, row-major
+  T* sT = sE + NE * NE;                  // E_f P
+  T* sR = sT + NE * NE;                  // result
+  __shared__ T p2[2][3][3], p1[2][3][3];  // [offset][child node][parent node] (p1 uses 2 x 2)
+  if (threadIdx.x < 18) {
+    const int o = threadIdx.x / 9, i = (threadIdx.x / 3) % 3, a = threadIdx.x % 3;
+    p2[o][i][a] = (T)tab[(2 * o + i) * 3 + a];
+    p1[o][i][a] = (i < 2 && a < 2) ? (T)tab[15 + (o + i) * 2 + a] : (T)0;
+  }
+  __syncthreads();
+  const long ncell = (long)ncx * ncy * ncz;
+  const int nfx = 2 * ncx, nfy = 2 * ncy;
+  constexpr int NSEG = NC + 1;  // velocity component blocks + the pressure block
+  for (long item = blockIdx.x; item < ncell * K1; item += gridDim.x) {
+    const long cc = item / K1;
+    const int mu = (int)(item % K1);
+    const int cx = (int)(cc % ncx), cy = (int)((cc / ncx) % ncy), cz = (int)(cc / ((long)ncx * ncy));
+    for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) sR[i] = 0;
+    for (int ch = 0; ch < (1 << DIM); ++ch) {
+      const int off[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+      const long fcell = (2 * cx + off[0]) + (long)nfx * ((2 * cy + off[1]) + (long)nfy * (DIM == 3 ? 2 * cz + off[2] : 0));
+      const T* src = Ef + (fcell * K1 + mu) * NE * NE;
+      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) sE[i] = src[i];
+      __syncthreads();
+      // T[r][seg] = P_seg^T E[r][seg]  (row segments)
+      for (int t = threadIdx.x; t < NE * NSEG; t += blockDim.x) {
+        const int r = t / NSEG, sg = t % NSEG;
+        if (sg < NC) galerkin_segment<DIM, 3, T, false>(sE + r * NE + sg * NQ, sT + r * NE + sg * NQ, 1, p2, off);
+        else galerkin_segment<DIM, 2, T, false>(sE + r * NE + NC * NQ, sT + r * NE + NC * NQ, 1, p1, off);
+      }
+      __syncthreads();
+      // R[seg][b] += P_seg^T T[seg][b]  (column segments)
+      for (int t = threadIdx.x; t < NE * NSEG; t += blockDim.x) {
+        const int b = t / NSEG, sg = t % NSEG;
+        if (sg < NC) galerkin_segment<DIM, 3, T, true>(sT + sg * NQ * NE + b, sR + sg * NQ * NE + b, NE, p2, off);
+        else galerkin_segment<DIM, 2, T, true>(sT + NC * NQ * NE + b, sR + NC * NQ * NE + b, NE, p1, off);
+      }
+      __syncthreads();
+    }
+    T* dst = Ec + (cc * K1 + mu) * NE * NE;
+    for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) dst[i] = sR[i];
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------- patch assembly
 // A_K (N x N, column-major F[col][row]) for cell K:
 //   block (mu, nu): K_t[mu][nu] M_K (velocity part) + delta_{mu nu} S_mu,
@@ -1149,23 +1244,23 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
     const unsigned g = (unsigned)(items < 4L * h->nsm ? items : 4L * h->nsm);
     if (prec == ST_FP64) {
       if (h->dim == 2) {
-        cudaFuncSetAttribute(galerkin_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        galerkin_kernel<2, double><<<g, 256, sm, h->stream>>>((const double*)m->L[l + 1].E, (double*)m->L[l].E,
-                                                              C.n[0], C.n[1], 1, K1, m->d_pch);
+        cudaFuncSetAttribute(galerkin_sf_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_sf_kernel<2, double><<<g, 256, sm, h->stream>>>((const double*)m->L[l + 1].E, (double*)m->L[l].E,
+                                                                 C.n[0], C.n[1], 1, K1, m->d_tab);
       } else {
-        cudaFuncSetAttribute(galerkin_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        galerkin_kernel<3, double><<<g, 256, sm, h->stream>>>((const double*)m->L[l + 1].E, (double*)m->L[l].E,
-                                                              C.n[0], C.n[1], C.n[2], K1, m->d_pch);
+        cudaFuncSetAttribute(galerkin_sf_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_sf_kernel<3, double><<<g, 256, sm, h->stream>>>((const double*)m->L[l + 1].E, (double*)m->L[l].E,
+                                                                 C.n[0], C.n[1], C.n[2], K1, m->d_tab);
       }
     } else {
       if (h->dim == 2) {
-        cudaFuncSetAttribute(galerkin_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        galerkin_kernel<2, float><<<g, 256, sm, h->stream>>>((const float*)m->L[l + 1].E, (float*)m->L[l].E, C.n[0],
-                                                             C.n[1], 1, K1, m->d_pch);
+        cudaFuncSetAttribute(galerkin_sf_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_sf_kernel<2, float><<<g, 256, sm, h->stream>>>((const float*)m->L[l + 1].E, (float*)m->L[l].E,
+                                                                C.n[0], C.n[1], 1, K1, m->d_tab);
       } else {
-        cudaFuncSetAttribute(galerkin_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        galerkin_kernel<3, float><<<g, 256, sm, h->stream>>>((const float*)m->L[l + 1].E, (float*)m->L[l].E, C.n[0],
-                                                             C.n[1], C.n[2], K1, m->d_pch);
+        cudaFuncSetAttribute(galerkin_sf_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        galerkin_sf_kernel<3, float><<<g, 256, sm, h->stream>>>((const float*)m->L[l + 1].E, (float*)m->L[l].E,
+                                                                C.n[0], C.n[1], C.n[2], K1, m->d_tab);
       }
     }
     e = cudaGetLastError();

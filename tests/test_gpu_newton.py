@@ -81,3 +81,25 @@ def test_newton_failure_paths_keep_handle_usable():
     status, info = st.Problem(p).newton_step(st.ST_MODN, dev(U0), dev(vprev))
     assert status == st.ST_OK
     prob.residual(dev(U0), dev(vprev))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_channel_newton_final_residual_by_oracle(prec):
+    # the channel flow of the Newton benchmark on a 32x8x8 mesh, first slab
+    # from rest: the GPU step (FP64 or FP32 V-cycle) reaches |R|_M <= 1e-8
+    # |R0|_M, and the oracle's residual at the GPU's solution agrees
+    st = gpu()
+    p = si.config(5, nx=32, ny=8, nz=8, p=1.5, delta=1e-3, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=4,
+                  newton_maxit=30)
+    s = oracle.sizes(p)
+    prob = st.Problem(p)
+    U = torch.zeros(prob.num_dofs(), dtype=torch.float64, device="cuda")
+    vprev = torch.zeros(s["Mv"], dtype=torch.float64, device="cuda")
+    status, info = prob.newton_step(st.ST_MODN, U, vprev, vcycle_prec=prec)
+    assert status == st.ST_OK
+    r0 = np.sqrt(oracle.mnorm2(p, oracle.residual(p, np.zeros(s["Nst"]), vprev=np.zeros(s["Mv"]))))
+    rf = np.sqrt(oracle.mnorm2(p, oracle.residual(p, U.cpu().numpy(), vprev=np.zeros(s["Mv"]))))
+    assert abs(r0 - info["res_norm_initial"]) <= 1e-12 * r0
+    assert rf <= 1.0001e-8 * r0, (rf / r0, info)
+    prob.close()
+

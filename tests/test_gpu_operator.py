@@ -138,6 +138,27 @@ def test_full_size_sampled_rows_config2():
     assert np.abs(Rg - Rr).max() / np.abs(Rr).max() <= TOL64
 
 
+def test_full_size_sampled_rows_64cube_k2():
+    # the largest mesh of the workloads: 64^3 hexes, dG(2) (20.1 M space-time
+    # dofs), FP64 and FP32, sampled outputs against the oracle
+    p = si.config(3)
+    st = gpu()
+    prob = st.Problem(p)
+    s = oracle.sizes(p)
+    U = si.fourier_state(p, 0)
+    dU = si.uniform_state(p, 1)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([rng.integers(0, s["Nst"], 32), [0, s["Nst"] - 1]]))
+    cells = oracle.cells_touching(p, rows)
+    Jr = oracle.jacobian_apply(p, oracle.MODN, U, dU, cells=cells)[rows]
+    prob.linearize(st.ST_MODN, dev(U))
+    Jg = prob.jacobian_apply(st.ST_MODN, dev(dU)).cpu().numpy()[rows]
+    assert np.abs(Jg - Jr).max() / np.abs(Jr).max() <= TOL64
+    Jg32 = prob.jacobian_apply(st.ST_MODN, dev(dU, torch.float32), prec=st.ST_FP32).double().cpu().numpy()[rows]
+    assert np.abs(Jg32 - Jr).max() / np.abs(Jr).max() <= TOL32
+    prob.close()
+
+
 def test_mnorm_matches_oracle():
     p = si.base_params(dim=3, nx=3, ny=2, nz=4, k=2)
     r = si.uniform_state(p, 7)
