@@ -38,6 +38,22 @@ struct TimeTab {
 void make_ref_tables(RefTables& R);
 bool make_time_tables(int k, TimeTab& T);
 
+// Diagonalisation of the finest-level surrogate patch in time.  With
+// W = diag(w_mu / w_0) the surrogate patch is (W (x) I)(B (x) M_v + I (x) S),
+// B = W^{-1} K_t = X diag(lambda) X^{-1}, so its inverse is
+// (X (x) I) diag_i((lambda_i M_v + S)^{-1}) (X^{-1} W^{-1} (x) I).  One block
+// is kept per real eigenvalue and per complex-conjugate pair (the pair's
+// second block is the conjugate for real data):
+//   s_b = sum_mu tin[b][mu] r_mu,  z_b = (lambda_b M_v + S)^{-1} s_b,
+//   x_mu = sum_b Re(tout[b][mu] z_b)   (tout carries the factor 2 of a pair).
+struct TimeEig {
+  int nb = 0;                       // kept blocks
+  double lam[MAX_K1][2];            // eigenvalue (re, im)
+  double tin[MAX_K1][MAX_K1][2];    // rows of X^{-1} W^{-1}
+  double tout[MAX_K1][MAX_K1][2];   // columns of X (x2 for a pair), [b][mu]
+};
+bool make_time_eig(const TimeTab& T, TimeEig& out);
+
 // ----------------------------------------------------------- kernel args
 struct OpArgs {
   int n[3];

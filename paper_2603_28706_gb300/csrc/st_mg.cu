@@ -280,6 +280,9 @@ struct PatchArgs {
   double wr[4];        // w_mu / w_0 (surrogate) or 1
   double M1h[3][9];    // 1D Q2 mass matrices scaled by h
   int surrogate;
+  int c13;             // surrogate patch diagonalised in time: nb complex blocks lambda_b M_v + S
+  int nb;
+  double lam[4][2];
 };
 
 template <int DIM>
@@ -314,7 +317,7 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
   for (long K = blockIdx.x; K < ncell; K += gridDim.x) {
     const int k3[3] = {(int)(K % pa.n[0]), (int)((K / pa.n[0]) % pa.n[1]),
                        DIM == 3 ? (int)(K / ((long)pa.n[0] * pa.n[1])) : 0};
-    T* Fk = F + K * (long)N * N;
+    T* Fk = F + K * (pa.c13 ? (long)pa.nb * NE * NE * 2 : (long)N * N);
     for (int it = threadIdx.x; it < NE * NE; it += blockDim.x) {
       const int p = it / NE, q = it % NE;  // row, column within a spatial block
       // spatial block sums (per mu) and the velocity mass entry
@@ -346,6 +349,15 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
               mass += m;
             }
           }
+      if (pa.c13) {
+        // block b: lambda_b M_v + S_0 (S_0: the surrogate block of node 0), complex, column-major
+        for (int b = 0; b < pa.nb; ++b) {
+          T* g = Fk + ((long)(b * NE + q) * NE + p) * 2;
+          g[0] = S[0] + (vel_pair ? (T)(pa.lam[b][0] * mass) : (T)0);
+          g[1] = vel_pair ? (T)(pa.lam[b][1] * mass) : (T)0;
+        }
+        continue;
+      }
       for (int mu = 0; mu < K1; ++mu)
         for (int nu = 0; nu < K1; ++nu) {
           T v = (mu == nu) ? S[mu] : (T)0;
@@ -699,6 +711,263 @@ inline bool try_gj_reg(float* F, int* piv, int N, long count, int* err, int nsm,
   return false;
 }
 
+// The register Gauss-Jordan inversion (implicit pivoting, see
+// gj_invert_reg_kernel) for complex matrices stored as interleaved (re, im)
+// pairs, column-major; R = float or double; pivot: largest |a_ik|^2.
+template <int RPL, int CPW, int NW, typename R>
+__global__ void __launch_bounds__(32 * NW) gj_invert_reg_cplx(R* __restrict__ F, int N, long count,
+                                                              int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char gc_raw[];
+  R* S = reinterpret_cast<R*>(gc_raw);                          // 2 N^2 staging of the result
+  R* s_col = S + 2 * (size_t)N * N;                              // column k (2 x 32 RPL)
+  R* s_row = s_col + 2 * 32 * RPL;                               // pivot row (2 x NW CPW)
+  int* s_used = reinterpret_cast<int*>(s_row + 2 * NW * CPW);
+  int* s_kinv = s_used + 32 * RPL;
+  int* s_pv = s_kinv + 32 * RPL;
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (long m = blockIdx.x; m < count; m += gridDim.x) {
+    const R* G = F + m * 2 * (long)N * N;
+    R ar[RPL][CPW], ai[RPL][CPW];
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const int j = w + NW * c;
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        const bool in = i < N && j < N;
+        ar[r][c] = in ? G[((long)j * N + i) * 2] : (R)0;
+        ai[r][c] = in ? G[((long)j * N + i) * 2 + 1] : (R)0;
+      }
+    }
+    for (int i = threadIdx.x; i < 32 * RPL; i += blockDim.x) s_used[i] = (i < N) ? 0 : 1;
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+      const int wk = k % NW, ck = k / NW;
+      if (w == wk) {
+        R best = (R)-1;
+        int bi = 0x7fffffff;
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+          if (c == ck) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+              const int i = lane + 32 * r;
+              s_col[2 * i] = ar[r][c];
+              s_col[2 * i + 1] = ai[r][c];
+              if (i < N && !s_used[i]) {
+                if (bi == 0x7fffffff) bi = i;
+                const R v = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+                if (v > best) {
+                  best = v;
+                  bi = i;
+                }
+              }
+            }
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+          }
+        }
+        if (lane == 0) {
+          s_p = bi;
+          s_used[bi] = 1;
+          s_kinv[bi] = k;
+          s_pv[k] = bi;
+          if (!(best > (R)0)) atomicExch(err, 1);
+        }
+      }
+      __syncthreads();
+      const int p = s_p, lp = p & 31, rp = p >> 5;
+      if (lane == lp) {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+          if (r == rp) {
+#pragma unroll
+            for (int c = 0; c < CPW; ++c) {
+              s_row[2 * (w + NW * c)] = ar[r][c];
+              s_row[2 * (w + NW * c) + 1] = ai[r][c];
+            }
+          }
+      }
+      __syncthreads();
+      const R dr = s_row[2 * k], di = s_row[2 * k + 1], dn = dr * dr + di * di;
+      const R ir = dr / dn, ii = -di / dn;  // 1 / d
+      R fr[RPL], fi[RPL];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        fr[r] = s_col[2 * (lane + 32 * r)];
+        fi[r] = s_col[2 * (lane + 32 * r) + 1];
+      }
+      if (lane == lp) {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r)
+          if (r == rp) {
+            fr[r] = 0;
+            fi[r] = 0;
+          }
+      }
+      if (w == wk) {
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+          if (c == ck) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+              ar[r][c] = 0;
+              ai[r][c] = 0;
+            }
+          }
+      }
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const int j = w + NW * c;
+        R xr = s_row[2 * j], xi = s_row[2 * j + 1];
+        if (j == k) {
+          xr = 1;
+          xi = 0;
+        }
+        const R rr = xr * ir - xi * ii, ri = xr * ii + xi * ir;  // a_pj / d (1/d at j = k)
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          ar[r][c] = fma(-fr[r], rr, fma(fi[r], ri, ar[r][c]));
+          ai[r][c] = fma(-fr[r], ri, fma(-fi[r], rr, ai[r][c]));
+        }
+        if (lane == lp) {
+#pragma unroll
+          for (int r = 0; r < RPL; ++r)
+            if (r == rp) {
+              ar[r][c] = rr;
+              ai[r][c] = ri;
+            }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const int j = w + NW * c;
+      if (j < N) {
+        const int dc = s_pv[j];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
+          if (i < N) {
+            S[((long)dc * N + s_kinv[i]) * 2] = ar[r][c];
+            S[((long)dc * N + s_kinv[i]) * 2 + 1] = ai[r][c];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    R* Go = F + m * 2 * (long)N * N;
+    for (long t = threadIdx.x; t < 2 * (long)N * N; t += blockDim.x) Go[t] = S[t];
+    __syncthreads();
+  }
+}
+
+template <int RPL, int CPW, typename R>
+cudaError_t launch_gj_cplx(R* F, int N, long count, int* err, int nsm, cudaStream_t st) {
+  constexpr int NW = 16;
+  const size_t sm = 2 * (size_t)N * N * sizeof(R) + 2 * (32 * RPL + NW * CPW) * sizeof(R) + 3 * 32 * RPL * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(gj_invert_reg_cplx<RPL, CPW, NW, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int occ = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gj_invert_reg_cplx<RPL, CPW, NW, R>, 32 * NW, sm);
+  if (e != cudaSuccess) return e;
+  const long cap = (long)(occ > 0 ? occ : 1) * nsm;
+  const unsigned g = (unsigned)(count < cap ? count : cap);
+  gj_invert_reg_cplx<RPL, CPW, NW, R><<<g, 32 * NW, sm, st>>>(F, N, count, err);
+  return cudaGetLastError();
+}
+
+// complex patches of the time-diagonalised surrogate (N = NE: 22 in 2D, 89 in 3D)
+template <typename R>
+cudaError_t invert_patches_cplx(R* F, int N, long count, int* err, int nsm, cudaStream_t st) {
+  if (N <= 32) return launch_gj_cplx<1, 2, R>(F, N, count, err, nsm, st);
+  if (N <= 96) return launch_gj_cplx<3, 6, R>(F, N, count, err, nsm, st);
+  return cudaErrorInvalidValue;
+}
+
+// Time-diagonalised surrogate patch solve (see TimeEig): for the patches of
+// one colour class, s_b = sum_mu tin[b][mu] r_mu, z_b = G_b^{-1} s_b (complex,
+// explicit inverse), x_mu = sum_b Re(tout[b][mu] z_b), d|_K += omega x.
+struct VankaC13 {
+  int nb;
+  double tin[MAX_K1][MAX_K1][2], tout[MAX_K1][MAX_K1][2];
+};
+
+template <int DIM, typename T>
+__global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int K1, const T* __restrict__ defect,
+                                      T* __restrict__ d, int n0, int n1, int n2, int c0x, int c0y, int c0z, int cnx,
+                                      int cny, long ncol, double omega, long Nq2, long Nq1, long Mv, long Mp) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
+  const int N = K1 * NE, nb = vc.nb;
+  __shared__ T sx[MAXN];
+  __shared__ long sg[MAXN];
+  __shared__ T ss[MAX_K1][NE][2], sz[MAX_K1][NE][2];
+  const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
+  for (long li = blockIdx.x; li < ncol; li += gridDim.x) {
+    const int ex = c0x + 2 * (int)(li % cnx), ey = c0y + 2 * (int)((li / cnx) % cny),
+              ez = DIM == 3 ? c0z + 2 * (int)(li / ((long)cnx * cny)) : 0;
+    const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
+    const T* Gk = G + cell * (long)nb * NE * NE * 2;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int mu = r / NE, loc = r % NE;
+      long g;
+      if (loc < NC * NQ) {
+        const int c = loc / NQ, q = loc % NQ;
+        g = (long)mu * Mv + c * Nq2 + (2L * ex + q % 3) + g2x * ((2L * ey + (q / 3) % 3) + g2y * (2L * ez + q / 9));
+      } else {
+        const int m = loc - NC * NQ;
+        g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+      }
+      sg[r] = g;
+      sx[r] = defect[g];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb * NE; t += blockDim.x) {
+      const int b = t / NE, q = t % NE;
+      T re = 0, im = 0;
+      for (int mu = 0; mu < K1; ++mu) {
+        const T x = sx[mu * NE + q];
+        re += (T)vc.tin[b][mu][0] * x;
+        im += (T)vc.tin[b][mu][1] * x;
+      }
+      ss[b][q][0] = re;
+      ss[b][q][1] = im;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb * NE; t += blockDim.x) {
+      const int b = t / NE, p = t % NE;
+      const T* gb = Gk + (long)b * NE * NE * 2 + 2 * p;
+      T re = 0, im = 0;
+#pragma unroll 4
+      for (int q = 0; q < NE; ++q) {
+        const T gr = gb[(long)q * NE * 2], gi = gb[(long)q * NE * 2 + 1];
+        const T sr = ss[b][q][0], si = ss[b][q][1];
+        re = fma(gr, sr, fma(-gi, si, re));
+        im = fma(gr, si, fma(gi, sr, im));
+      }
+      sz[b][p][0] = re;
+      sz[b][p][1] = im;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int mu = r / NE, p = r % NE;
+      T x = 0;
+      for (int b = 0; b < nb; ++b) x += (T)vc.tout[b][mu][0] * sz[b][p][0] - (T)vc.tout[b][mu][1] * sz[b][p][1];
+      d[sg[r]] += (T)omega * x;
+    }
+    __syncthreads();
+  }
+}
+
 // launch the shared-memory inversion when the matrix fits, else the global one
 template <typename T>
 cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
@@ -897,6 +1166,8 @@ struct MgState {
   int g_prec = -1, g_tangent = -1;
   bool g_seen = false;           // the key was run once eagerly (all lazy initialisation done)
   bool g_failed = false;         // capture failed for this key: eager
+  bool c13 = false;              // finest surrogate patches diagonalised in time (TimeEig)
+  TimeEig te;
 };
 
 namespace {
@@ -945,6 +1216,7 @@ void free_mg(MgState* m) {
 }
 
 cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
+  m->c13 = make_time_eig(h->T, m->te) && m->te.nb <= MAX_K1;
   const int nl = (int)h->lev.size();
   const int NE = ne_of(h->dim), K1 = h->K1, N = K1 * NE;
   const size_t es = esz(prec);
@@ -954,7 +1226,10 @@ cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
     const Level& Lv = h->lev[l];
     MgLevelData& d = m->L[l];
     e = cudaMalloc(&d.E, (size_t)Lv.ncells * K1 * NE * NE * es);
-    if (e == cudaSuccess) e = cudaMalloc(&d.LU, (size_t)Lv.ncells * N * N * es);
+    // finest level with the time-diagonalised surrogate: nb complex NE x NE inverses per patch
+    const bool c13 = (l == nl - 1) && m->c13;
+    const size_t nlu = c13 ? (size_t)m->te.nb * NE * NE * 2 : (size_t)N * N;
+    if (e == cudaSuccess) e = cudaMalloc(&d.LU, (size_t)Lv.ncells * nlu * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.piv, (size_t)Lv.ncells * N * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&d.r, (size_t)Lv.Nst * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.d, (size_t)Lv.Nst * es);
@@ -1079,6 +1354,25 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
       if (ncol == 0) continue;
       const unsigned g = (unsigned)(ncol < 16L * h->nsm ? ncol : 16L * h->nsm);
       const int nt = N <= 128 ? 128 : 256;
+      if (m->c13 && l == (int)h->lev.size() - 1) {
+        VankaC13 vc;
+        vc.nb = m->te.nb;
+        memcpy(vc.tin, m->te.tin, sizeof(vc.tin));
+        memcpy(vc.tout, m->te.tout, sizeof(vc.tout));
+        if (h->dim == 2)
+          vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, d, L.n[0],
+                                                               L.n[1], L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2],
+                                                               L.cn[c][0], L.cn[c][1], ncol, h->P.omega, L.Nq2,
+                                                               L.Nq1, L.Mv, L.Mp);
+        else
+          vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, d, L.n[0],
+                                                               L.n[1], L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2],
+                                                               L.cn[c][0], L.cn[c][1], ncol, h->P.omega, L.Nq2,
+                                                               L.Nq1, L.Mv, L.Mp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        continue;
+      }
       if (h->dim == 2)
         vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
                                                          L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
@@ -1273,21 +1567,33 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
     const bool sur = (l == L);
     if (sur && !rebuild_finest) continue;  // refresh rule: keep the surrogate factorisations
     PatchArgs pa = patch_args(h, l, sur);
+    const bool c13 = sur && m->c13;
+    if (c13) {
+      pa.c13 = 1;
+      pa.nb = m->te.nb;
+      for (int b = 0; b < m->te.nb; ++b) {
+        pa.lam[b][0] = m->te.lam[b][0];
+        pa.lam[b][1] = m->te.lam[b][1];
+      }
+    }
     const void* Esrc = sur ? m->Erep : m->L[l].E;
     const int estride = sur ? 1 : K1;
     const unsigned g = (unsigned)(Lv.ncells < 8L * h->nsm ? Lv.ncells : 8L * h->nsm);
+    const long nblk = Lv.ncells * (long)m->te.nb;
     if (prec == ST_FP64) {
       if (h->dim == 2) patch_assemble<2, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
       else patch_assemble<3, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        e = invert_patches<double>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
+        e = c13 ? invert_patches_cplx<double>((double*)m->L[l].LU, NE, nblk, h->d_err, h->nsm, h->stream)
+                : invert_patches<double>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
     } else {
       if (h->dim == 2) patch_assemble<2, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       else patch_assemble<3, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        e = invert_patches<float>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
+        e = c13 ? invert_patches_cplx<float>((float*)m->L[l].LU, NE, nblk, h->d_err, h->nsm, h->stream)
+                : invert_patches<float>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
   }

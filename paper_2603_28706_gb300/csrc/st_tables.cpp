@@ -8,6 +8,7 @@
 // monomial coefficients of the Lagrange basis.
 
 #include <cmath>
+#include <complex>
 
 #include "st_internal.h"
 
@@ -191,6 +192,188 @@ bool make_time_tables(int k, TimeTab& T) {
       for (int m = 1; m < n; ++m)
         for (int l = 0; l < n; ++l) v += C[j][m] * m * C[i][l] / (double)(m + l);
       T.Kt[i * n + j] = v + C[j][0] * C[i][0];
+    }
+  }
+  return true;
+}
+
+
+// ---------------------------------------------------------------------
+// Eigen-decomposition of B = W^{-1} K_t (K1 <= 4, real, non-symmetric):
+// characteristic polynomial by the Faddeev-LeVerrier recursion, its roots by
+// the Durand-Kerner (Weierstrass) iteration, eigenvectors as null vectors of
+// B - lambda I (complex elimination with full pivoting), X^{-1} by
+// Gauss-Jordan; checked by |X diag(lambda) X^{-1} - B| <= 1e-10 |B|.
+namespace {
+
+using cd = std::complex<double>;
+
+bool cinvert(int n, cd A[MAX_K1][MAX_K1], cd Ai[MAX_K1][MAX_K1]) {
+  cd M[MAX_K1][2 * MAX_K1];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) M[i][j] = j < n ? A[i][j] : cd(i == j - n ? 1.0 : 0.0);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(M[i][k]) > std::abs(M[p][k])) p = i;
+    if (std::abs(M[p][k]) == 0.0) return false;
+    for (int j = 0; j < 2 * n; ++j) std::swap(M[k][j], M[p][j]);
+    const cd d = M[k][k];
+    for (int j = 0; j < 2 * n; ++j) M[k][j] /= d;
+    for (int i = 0; i < n; ++i)
+      if (i != k) {
+        const cd f = M[i][k];
+        for (int j = 0; j < 2 * n; ++j) M[i][j] -= f * M[k][j];
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ai[i][j] = M[i][j + n];
+  return true;
+}
+
+// a null vector of the n x n matrix A (rank n - 1), largest entry 1
+void null_vector(int n, cd A[MAX_K1][MAX_K1], cd v[MAX_K1]) {
+  cd M[MAX_K1][MAX_K1];
+  int col[MAX_K1];
+  for (int i = 0; i < n; ++i) {
+    col[i] = i;
+    for (int j = 0; j < n; ++j) M[i][j] = A[i][j];
+  }
+  for (int k = 0; k < n - 1; ++k) {  // full pivoting on the leading n-1 steps
+    int pi = k, pj = k;
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j)
+        if (std::abs(M[i][j]) > std::abs(M[pi][pj])) {
+          pi = i;
+          pj = j;
+        }
+    for (int j = 0; j < n; ++j) std::swap(M[k][j], M[pi][j]);
+    for (int i = 0; i < n; ++i) std::swap(M[i][k], M[i][pj]);
+    std::swap(col[k], col[pj]);
+    for (int i = k + 1; i < n; ++i) {
+      const cd f = M[i][k] / M[k][k];
+      for (int j = k; j < n; ++j) M[i][j] -= f * M[k][j];
+    }
+  }
+  cd y[MAX_K1];
+  y[n - 1] = 1.0;
+  for (int k = n - 2; k >= 0; --k) {
+    cd acc = 0.0;
+    for (int j = k + 1; j < n; ++j) acc += M[k][j] * y[j];
+    y[k] = -acc / M[k][k];
+  }
+  double big = 0.0;
+  int ib = 0;
+  for (int i = 0; i < n; ++i) {
+    v[col[i]] = y[i];
+  }
+  for (int i = 0; i < n; ++i)
+    if (std::abs(v[i]) > big) {
+      big = std::abs(v[i]);
+      ib = i;
+    }
+  const cd s = v[ib];
+  for (int i = 0; i < n; ++i) v[i] /= s;
+}
+
+}  // namespace
+
+bool make_time_eig(const TimeTab& T, TimeEig& out) {
+  const int n = T.k + 1;
+  double B[MAX_K1][MAX_K1];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) B[i][j] = T.Kt[i * n + j] * T.w[0] / T.w[i];
+  // characteristic polynomial lambda^n + c[n-1] lambda^{n-1} + .. + c[0]
+  double c[MAX_K1 + 1];
+  {
+    double Mk[MAX_K1][MAX_K1] = {}, AM[MAX_K1][MAX_K1];
+    c[n] = 1.0;
+    for (int k = 1; k <= n; ++k) {
+      // M_k = B M_{k-1} + c_{n-k+1} I, c_{n-k} = -tr(B M_k) / k
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          double acc = 0.0;
+          for (int l = 0; l < n; ++l) acc += B[i][l] * Mk[l][j];
+          AM[i][j] = acc + (i == j ? c[n - k + 1] : 0.0);
+        }
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Mk[i][j] = AM[i][j];
+      double tr = 0.0;
+      for (int i = 0; i < n; ++i)
+        for (int l = 0; l < n; ++l) tr += B[i][l] * Mk[l][i];
+      c[n - k] = -tr / k;
+    }
+  }
+  cd z[MAX_K1];
+  for (int i = 0; i < n; ++i) z[i] = std::pow(cd(0.4, 0.9), i) * 2.0;
+  for (int it = 0; it < 500; ++it) {
+    double moved = 0.0;
+    for (int i = 0; i < n; ++i) {
+      cd pv = 1.0;
+      for (int k = n - 1; k >= 0; --k) pv = pv * z[i] + c[k];
+      cd den = 1.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) den *= (z[i] - z[j]);
+      const cd dz = pv / den;
+      z[i] -= dz;
+      moved = std::max(moved, std::abs(dz));
+    }
+    if (moved < 1e-15) break;
+  }
+  double bn = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) bn = std::max(bn, std::fabs(B[i][j]));
+  // order: real eigenvalues first, then each pair as (im > 0, conjugate)
+  cd lam[MAX_K1];
+  int cnt = 0;
+  bool used[MAX_K1] = {};
+  for (int i = 0; i < n; ++i)
+    if (std::fabs(z[i].imag()) <= 1e-10 * bn) {
+      lam[cnt++] = cd(z[i].real(), 0.0);
+      used[i] = true;
+    }
+  const int nreal = cnt;
+  for (int i = 0; i < n; ++i)
+    if (!used[i] && z[i].imag() > 0.0) {
+      lam[cnt++] = z[i];
+      lam[cnt++] = std::conj(z[i]);
+    }
+  if (cnt != n) return false;
+  cd X[MAX_K1][MAX_K1], Xi[MAX_K1][MAX_K1];
+  for (int e = 0; e < n; ++e) {
+    cd A[MAX_K1][MAX_K1], v[MAX_K1];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) A[i][j] = cd(B[i][j]) - (i == j ? lam[e] : cd(0.0));
+    null_vector(n, A, v);
+    if (e < nreal)
+      for (int i = 0; i < n; ++i) v[i] = cd(v[i].real(), 0.0);
+    if (e >= nreal && ((e - nreal) & 1))  // the conjugate of the previous one
+      for (int i = 0; i < n; ++i) v[i] = std::conj(X[i][e - 1]);
+    for (int i = 0; i < n; ++i) X[i][e] = v[i];
+  }
+  if (!cinvert(n, X, Xi)) return false;
+  double err = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      cd acc = 0.0;
+      for (int e = 0; e < n; ++e) acc += X[i][e] * lam[e] * Xi[e][j];
+      err = std::max(err, std::abs(acc - B[i][j]));
+    }
+  if (!(err <= 1e-10 * (bn > 0 ? bn : 1.0))) return false;
+  out.nb = 0;
+  for (int e = 0; e < n; ++e) {
+    const bool pair = e >= nreal;
+    if (pair && ((e - nreal) & 1)) continue;  // kept: the first of a pair
+    const int b = out.nb++;
+    out.lam[b][0] = lam[e].real();
+    out.lam[b][1] = lam[e].imag();
+    for (int mu = 0; mu < n; ++mu) {
+      const cd ti = Xi[e][mu] * (T.w[0] / T.w[mu]);  // X^{-1} W^{-1}
+      const cd to = X[mu][e] * (pair ? 2.0 : 1.0);
+      out.tin[b][mu][0] = ti.real();
+      out.tin[b][mu][1] = ti.imag();
+      out.tout[b][mu][0] = to.real();
+      out.tout[b][mu][1] = to.imag();
     }
   }
   return true;
