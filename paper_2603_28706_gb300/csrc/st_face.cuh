@@ -534,6 +534,7 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_matrix(const OpArgs a, con
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sW = reinterpret_cast<T*>(smem_raw);  // NE workspaces of PS entries
   __shared__ double sDn[9];                // Q2 basis derivative at the Gauss points, [q][a]
+  __shared__ T stab[D::NQ][D::NFQ][4];     // test functions of the face: value, normal and tangential derivatives
   if (threadIdx.x < 9) {
     const int q = threadIdx.x / 3, aa = threadIdx.x % 3;
     double v = 0.0;
@@ -591,6 +592,21 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_matrix(const OpArgs a, con
         else if constexpr (DIM == 3) face_point<DIM, K1, T, OP_JAC, TAN, 2>(a, w, fq, side, mu, cell, fid);
       }
       __syncthreads();
+      // test-function values and derivatives at the face points (all velocity nodes of the cell)
+      for (int it = threadIdx.x; it < NQ * NFQ; it += blockDim.x) {
+        const int n = it / NFQ, fq = it % NFQ;
+        const int nn[3] = {n % 3, (n / 3) % 3, (DIM == 3) ? n / 9 : 0};
+        const int i1 = fq % 3, i2 = (DIM == 3) ? fq / 3 : 0;
+        const double en = cT.E[up * 3 + nn[ax]], edn = cT.ED[up * 3 + nn[ax]] * a.ih[ax];
+        const double b1 = cT.B[i1 * 3 + nn[t1]], d1 = sDn[i1 * 3 + nn[t1]] * a.ih[t1];
+        const double b2 = (DIM == 3) ? cT.B[i2 * 3 + nn[t2]] : 1.0;
+        const double d2 = (DIM == 3) ? sDn[i2 * 3 + nn[t2]] * a.ih[t2] : 0.0;
+        stab[n][fq][0] = (T)(en * b1 * b2);
+        stab[n][fq][1] = (T)(edn * b1 * b2);
+        stab[n][fq][2] = (T)(en * d1 * b2);
+        stab[n][fq][3] = (T)(en * b1 * d2);
+      }
+      __syncthreads();
       // (3) integrate against every test function: E[i][j] += ...
       T* Ec = E + ((long)cell * a.elm_stride + a.elm_slot) * NE * NE;
       for (int it = threadIdx.x; it < NE * NE; it += blockDim.x) {
@@ -603,13 +619,10 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_matrix(const OpArgs a, con
           const double en = cT.E[up * 3 + nn[ax]], edn = cT.ED[up * 3 + nn[ax]] * a.ih[ax];
           if (en == 0.0 && edn == 0.0) continue;
           for (int fq = 0; fq < NFQ; ++fq) {
-            const int i1 = fq % 3, i2 = (DIM == 3) ? fq / 3 : 0;
-            const double b1 = cT.B[i1 * 3 + nn[t1]], d1 = sDn[i1 * 3 + nn[t1]] * a.ih[t1];
-            const double b2 = (DIM == 3) ? cT.B[i2 * 3 + nn[t2]] : 1.0;
-            const double d2 = (DIM == 3) ? sDn[i2 * 3 + nn[t2]] * a.ih[t2] : 0.0;
-            acc += w[Cfg::oPV + c * NFQ + fq] * (T)(en * b1 * b2) + w[Cfg::oPN + c * NFQ + fq] * (T)(edn * b1 * b2) +
-                   w[Cfg::oPT + (c * (DIM - 1) + 0) * NFQ + fq] * (T)(en * d1 * b2);
-            if (DIM == 3) acc += w[Cfg::oPT + (c * (DIM - 1) + 1) * NFQ + fq] * (T)(en * b1 * d2);
+            const T* tb = stab[n][fq];
+            acc += w[Cfg::oPV + c * NFQ + fq] * tb[0] + w[Cfg::oPN + c * NFQ + fq] * tb[1] +
+                   w[Cfg::oPT + (c * (DIM - 1) + 0) * NFQ + fq] * tb[2];
+            if (DIM == 3) acc += w[Cfg::oPT + (c * (DIM - 1) + 1) * NFQ + fq] * tb[3];
           }
         } else {
           const int m = i - NC * NQ;

@@ -370,6 +370,36 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
   }
 }
 
+// Colour classes of a level for one launch over all its cells in colour
+// order: class c holds the cells (c_x + 2 i, c_y + 2 j, c_z + 2 l); cells of
+// one class share no dof, so each class writes its own buffer (cb + c*stride)
+// with plain stores and colour_sum adds the buffers afterwards.
+struct ColourMap {
+  long start[9];
+  int cn[8][3];
+  int nclass;
+};
+
+__device__ __forceinline__ void colour_cell(const ColourMap& cm, long li, int& c, int& ex, int& ey, int& ez) {
+  c = 0;
+  for (int cc = 1; cc < cm.nclass; ++cc) c += (li >= cm.start[cc]) ? 1 : 0;
+  const long r = li - cm.start[c];
+  ex = (c & 1) + 2 * (int)(r % cm.cn[c][0]);
+  ey = ((c >> 1) & 1) + 2 * (int)((r / cm.cn[c][0]) % cm.cn[c][1]);
+  ez = ((c >> 2) & 1) + 2 * (int)(r / ((long)cm.cn[c][0] * cm.cn[c][1]));
+}
+
+// y = (accumulate ? y : 0) + alpha sum_c cb[c * stride + i]
+template <typename T>
+__global__ void colour_sum(const T* __restrict__ cb, long stride, int ncls, T* __restrict__ y, long n, T alpha,
+                           int accumulate) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    T acc = cb[i];
+    for (int c = 1; c < ncls; ++c) acc += cb[c * stride + i];
+    y[i] = (accumulate ? y[i] : (T)0) + alpha * acc;
+  }
+}
+
 // ------------------------------------------------------- batched inverse
 // In-place Gauss-Jordan inversion with partial (row) pivoting of `count`
 // matrices of size N stored column-major (F[col][row]); one CTA per matrix.
@@ -894,9 +924,9 @@ cudaError_t invert_patches_cplx(R* F, int N, long count, int* err, int nsm, cuda
   return cudaErrorInvalidValue;
 }
 
-// Time-diagonalised surrogate patch solve (see TimeEig): for the patches of
-// one colour class, s_b = sum_mu tin[b][mu] r_mu, z_b = G_b^{-1} s_b (complex,
-// explicit inverse), x_mu = sum_b Re(tout[b][mu] z_b), d|_K += omega x.
+// Time-diagonalised surrogate patch solve (see TimeEig), all patches in one
+// launch: s_b = sum_mu tin[b][mu] r_mu, z_b = G_b^{-1} s_b (complex, explicit
+// inverse), x_mu = sum_b Re(tout[b][mu] z_b) into the cell's colour buffer.
 struct VankaC13 {
   int nb;
   double tin[MAX_K1][MAX_K1][2], tout[MAX_K1][MAX_K1][2];
@@ -904,18 +934,19 @@ struct VankaC13 {
 
 template <int DIM, typename T>
 __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int K1, const T* __restrict__ defect,
-                                      T* __restrict__ d, int n0, int n1, int n2, int c0x, int c0y, int c0z, int cnx,
-                                      int cny, long ncol, double omega, long Nq2, long Nq1, long Mv, long Mp) {
+                                      T* __restrict__ cb, long cstride, int n0, int n1, int n2, ColourMap cm,
+                                      long ncells, long Nq2, long Nq1, long Mv, long Mp) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE, nb = vc.nb;
   __shared__ T sx[MAXN];
   __shared__ long sg[MAXN];
   __shared__ T ss[MAX_K1][NE][2], sz[MAX_K1][NE][2];
   const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
-  for (long li = blockIdx.x; li < ncol; li += gridDim.x) {
-    const int ex = c0x + 2 * (int)(li % cnx), ey = c0y + 2 * (int)((li / cnx) % cny),
-              ez = DIM == 3 ? c0z + 2 * (int)(li / ((long)cnx * cny)) : 0;
+  for (long li = blockIdx.x; li < ncells; li += gridDim.x) {
+    int col, ex, ey, ez;
+    colour_cell(cm, li, col, ex, ey, ez);
     const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
+    T* ob = cb + col * cstride;
     const T* Gk = G + cell * (long)nb * NE * NE * 2;
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
       const int mu = r / NE, loc = r % NE;
@@ -962,7 +993,7 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
       const int mu = r / NE, p = r % NE;
       T x = 0;
       for (int b = 0; b < nb; ++b) x += (T)vc.tout[b][mu][0] * sz[b][p][0] - (T)vc.tout[b][mu][1] * sz[b][p][1];
-      d[sg[r]] += (T)omega * x;
+      ob[sg[r]] = x;
     }
     __syncthreads();
   }
@@ -999,22 +1030,24 @@ cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm,
 }
 
 // ------------------------------------------------------------ Vanka solve
-// For the patches (cells) of one colour class: x = A_K^{-1} defect|_K with the
-// explicit inverse (a matrix-vector product streamed column by column), then
-// d|_K += omega x (cells of one class share no dof).
+// All patches (cells) in one launch: x = A_K^{-1} defect|_K with the explicit
+// inverse (a matrix-vector product streamed column by column), stored into
+// the buffer of the cell's colour class (cells of one class share no dof);
+// the caller adds omega times the class buffers into d.
 template <int DIM, typename T>
-__global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __restrict__ defect, T* __restrict__ d,
-                                  int n0, int n1, int n2, int c0x, int c0y, int c0z, int cnx, int cny, long ncol,
-                                  double omega, long Nq2, long Nq1, long Mv, long Mp) {
+__global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __restrict__ defect, T* __restrict__ cb,
+                                  long cstride, int n0, int n1, int n2, ColourMap cm, long ncells, long Nq2, long Nq1,
+                                  long Mv, long Mp) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE;
   __shared__ T sx[MAXN];
   __shared__ long sg[MAXN];
   const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
-  for (long li = blockIdx.x; li < ncol; li += gridDim.x) {
-    const int ex = c0x + 2 * (int)(li % cnx), ey = c0y + 2 * (int)((li / cnx) % cny),
-              ez = DIM == 3 ? c0z + 2 * (int)(li / ((long)cnx * cny)) : 0;
+  for (long li = blockIdx.x; li < ncells; li += gridDim.x) {
+    int col, ex, ey, ez;
+    colour_cell(cm, li, col, ex, ey, ez);
     const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
+    T* ob = cb + col * cstride;
     const T* A = F + cell * (long)N * N;
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
       const int mu = r / NE, loc = r % NE;
@@ -1034,30 +1067,41 @@ __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __re
       T acc = 0;
 #pragma unroll 8
       for (int j = 0; j < N; ++j) acc = fma(A[(long)j * N + r], sx[j], acc);
-      d[sg[r]] += (T)omega * acc;
+      ob[sg[r]] = acc;
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------- coarse-level apply
-// y += A_l x for the cells of one colour class: per cell and node mu the
-// element matrix E[cell][mu] (spatial part, times tau w_mu) and the temporal
-// mass coupling sum_nu K_t[mu][nu] M_e x_nu on the velocity.
+// (A_l x)|_K for all cells in one launch, into the buffer of the cell's
+// colour class: per cell and node mu the element matrix E[cell][mu] (spatial
+// part, times tau w_mu) and the temporal mass coupling sum_nu K_t[mu][nu]
+// M_e x_nu on the velocity; colour_sum forms A_l x.
 template <int DIM, typename T>
-__global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, const T* __restrict__ x, T* __restrict__ y,
-                             int c0x, int c0y, int c0z, int cnx, int cny, long ncol, long Nq2, long Nq1, long Mv,
-                             long Mp) {
+__global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, const T* __restrict__ x, T* __restrict__ cb,
+                             long cstride, ColourMap cm, long ncells, long Nq2, long Nq1, long Mv, long Mp) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   __shared__ T sx[MAXN];
   __shared__ long sg[MAXN];
+  __shared__ T smass[NQ * NQ];             // velocity mass of one cell (tensor of the 1D masses)
+  __shared__ T skt[MAX_K1][NC * NQ];       // sum_nu K_t[mu][nu] x_nu (velocity part)
   const int N = K1 * NE;
   const int n0 = pa.n[0], n1 = pa.n[1];
   const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
-  for (long li = blockIdx.x; li < ncol; li += gridDim.x) {
-    const int ex = c0x + 2 * (int)(li % cnx), ey = c0y + 2 * (int)((li / cnx) % cny),
-              ez = DIM == 3 ? c0z + 2 * (int)(li / ((long)cnx * cny)) : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) {
+    const int a = t / NQ, b = t % NQ;
+    const int ai[3] = {a % 3, (a / 3) % 3, a / 9}, bi[3] = {b % 3, (b / 3) % 3, b / 9};
+    double m = 1.0;
+    for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
+    smass[t] = (T)m;
+  }
+  for (long li = blockIdx.x; li < ncells; li += gridDim.x) {
+    int col, ex, ey, ez;
+    colour_cell(cm, li, col, ex, ey, ez);
     const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
+    T* ob = cb + col * cstride;
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
       const int mu = r / NE, loc = r % NE;
       long g;
@@ -1072,24 +1116,26 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
       sx[r] = x[g];
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    for (int t = threadIdx.x; t < K1 * NC * NQ; t += blockDim.x) {
+      const int mu = t / (NC * NQ), v = t % (NC * NQ);
+      T acc = 0;
+      for (int nu = 0; nu < K1; ++nu) acc += (T)pa.Kt[mu * K1 + nu] * sx[nu * NE + v];
+      skt[mu][v] = acc;
+    }
+    __syncthreads();
+    // one warp per row: coalesced row of E, then the temporal mass coupling
+    for (int r = warp; r < N; r += nwarp) {
       const int mu = r / NE, i = r % NE;
       const T* Er = E + (cell * K1 + mu) * NE * NE + (long)i * NE;
       T acc = 0;
-      for (int j = 0; j < NE; ++j) acc += Er[j] * sx[mu * NE + j];
+      for (int j = lane; j < NE; j += 32) acc = fma(Er[j], sx[mu * NE + j], acc);
       if (i < NC * NQ) {
         const int c = i / NQ, a = i % NQ;
-        const int ai[3] = {a % 3, (a / 3) % 3, a / 9};
-        for (int b = 0; b < NQ; ++b) {
-          const int bi[3] = {b % 3, (b / 3) % 3, b / 9};
-          double m = 1.0;
-          for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
-          T s = 0;
-          for (int nu = 0; nu < K1; ++nu) s += (T)pa.Kt[mu * K1 + nu] * sx[nu * NE + c * NQ + b];
-          acc += (T)m * s;
-        }
+        for (int bq = lane; bq < NQ; bq += 32) acc = fma(smass[a * NQ + bq], skt[mu][c * NQ + bq], acc);
       }
-      y[sg[r]] += acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) ob[sg[r]] = acc;
     }
     __syncthreads();
   }
@@ -1143,6 +1189,7 @@ struct MgLevelData {
   void* t = nullptr;
   void* t2 = nullptr;
   void* t3 = nullptr;
+  void* cbuf = nullptr;  // 2^d colour-private level vectors (zero outside each class's dofs)
 };
 
 struct MgState {
@@ -1194,6 +1241,7 @@ void free_mg(MgState* m) {
     cudaFree(l.t);
     cudaFree(l.t2);
     cudaFree(l.t3);
+    cudaFree(l.cbuf);
   }
   m->L.clear();
   cudaFree(m->Erep);
@@ -1236,6 +1284,8 @@ cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
     if (e == cudaSuccess) e = cudaMalloc(&d.t, (size_t)Lv.Nst * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.t2, (size_t)Lv.Nst * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.t3, (size_t)Lv.Nst * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.cbuf, (size_t)(1 << h->dim) * Lv.Nst * es);
+    if (e == cudaSuccess) e = cudaMemset(d.cbuf, 0, (size_t)(1 << h->dim) * Lv.Nst * es);
   }
   const Level& F = h->lev.back();
   if (e == cudaSuccess) e = cudaMalloc(&m->Erep, (size_t)F.ncells * NE * NE * es);
@@ -1313,29 +1363,35 @@ cudaError_t elm_dispatch(st_problem* h, int level, int prec, int tangent, const 
                      : dispatch_elm_3d(h, L, a, prec, tangent, E, bcells, nbc);
 }
 
+ColourMap colour_map(const st_problem* h, const Level& L) {
+  ColourMap cm;
+  cm.nclass = 1 << h->dim;
+  for (int c = 0; c < 9; ++c) cm.start[c] = L.col_start[c];
+  for (int c = 0; c < 8; ++c)
+    for (int d = 0; d < 3; ++d) cm.cn[c][d] = L.cn[c][d];
+  return cm;
+}
+
 template <typename T>
 cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
   // y = A_l x
   const Level& L = h->lev[l];
   const int prec = sizeof(T) == 8 ? ST_FP64 : ST_FP32;
   if (l == (int)h->lev.size() - 1) return launch_op(h, l, OP_JAC, prec, h->lin_tangent, x, y, nullptr, nullptr);
-  cudaError_t e = cudaMemsetAsync(y, 0, L.Nst * sizeof(T), h->stream);
-  if (e != cudaSuccess) return e;
   PatchArgs pa = patch_args(h, l, false);
-  for (int c = 0; c < (1 << h->dim); ++c) {
-    const long ncol = L.col_start[c + 1] - L.col_start[c];
-    if (ncol == 0) continue;
-    const unsigned g = (unsigned)(ncol < 8L * h->nsm ? ncol : 8L * h->nsm);
-    if (h->dim == 2)
-      coarse_apply<2, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, y, L.c0[c][0], L.c0[c][1],
-                                                   L.c0[c][2], L.cn[c][0], L.cn[c][1], ncol, L.Nq2, L.Nq1, L.Mv, L.Mp);
-    else
-      coarse_apply<3, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, y, L.c0[c][0], L.c0[c][1],
-                                                   L.c0[c][2], L.cn[c][0], L.cn[c][1], ncol, L.Nq2, L.Nq1, L.Mv, L.Mp);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const ColourMap cm = colour_map(h, L);
+  T* cb = (T*)m->L[l].cbuf;
+  const unsigned g = (unsigned)(L.ncells < 8L * h->nsm ? L.ncells : 8L * h->nsm);
+  if (h->dim == 2)
+    coarse_apply<2, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm, L.ncells, L.Nq2,
+                                                 L.Nq1, L.Mv, L.Mp);
+  else
+    coarse_apply<3, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm, L.ncells, L.Nq2,
+                                                 L.Nq1, L.Mv, L.Mp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, y, L.Nst, (T)1, 0);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -1349,41 +1405,36 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
     sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int c = 0; c < (1 << h->dim); ++c) {
-      const long ncol = L.col_start[c + 1] - L.col_start[c];
-      if (ncol == 0) continue;
-      const unsigned g = (unsigned)(ncol < 16L * h->nsm ? ncol : 16L * h->nsm);
-      const int nt = N <= 128 ? 128 : 256;
-      if (m->c13 && l == (int)h->lev.size() - 1) {
-        VankaC13 vc;
-        vc.nb = m->te.nb;
-        memcpy(vc.tin, m->te.tin, sizeof(vc.tin));
-        memcpy(vc.tout, m->te.tout, sizeof(vc.tout));
-        if (h->dim == 2)
-          vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, d, L.n[0],
-                                                               L.n[1], L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2],
-                                                               L.cn[c][0], L.cn[c][1], ncol, h->P.omega, L.Nq2,
-                                                               L.Nq1, L.Mv, L.Mp);
-        else
-          vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, d, L.n[0],
-                                                               L.n[1], L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2],
-                                                               L.cn[c][0], L.cn[c][1], ncol, h->P.omega, L.Nq2,
-                                                               L.Nq1, L.Mv, L.Mp);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        continue;
-      }
+    // all patches in one launch into the colour buffers, then d += omega sum
+    const ColourMap cm = colour_map(h, L);
+    T* cb = (T*)D.cbuf;
+    const unsigned g = (unsigned)(L.ncells < 16L * h->nsm ? L.ncells : 16L * h->nsm);
+    const int nt = N <= 128 ? 128 : 256;
+    if (m->c13 && l == (int)h->lev.size() - 1) {
+      VankaC13 vc;
+      vc.nb = m->te.nb;
+      memcpy(vc.tin, m->te.tin, sizeof(vc.tin));
+      memcpy(vc.tout, m->te.tout, sizeof(vc.tout));
       if (h->dim == 2)
-        vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
-                                                         L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
-                                                         L.cn[c][1], ncol, h->P.omega, L.Nq2, L.Nq1, L.Mv, L.Mp);
+        vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+                                                             L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv,
+                                                             L.Mp);
       else
-        vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, d, L.n[0], L.n[1],
-                                                         L.n[2], L.c0[c][0], L.c0[c][1], L.c0[c][2], L.cn[c][0],
-                                                         L.cn[c][1], ncol, h->P.omega, L.Nq2, L.Nq1, L.Mv, L.Mp);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+        vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+                                                             L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv,
+                                                             L.Mp);
+    } else if (h->dim == 2) {
+      vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+                                                       L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+    } else {
+      vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+                                                       L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, d, L.Nst, (T)h->P.omega, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
