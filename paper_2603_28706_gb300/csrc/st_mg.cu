@@ -584,28 +584,28 @@ __global__ void gj_invert_smem_kernel(T* __restrict__ F, int* __restrict__ piv, 
 // memory.  Thread (lane, warp) holds rows lane + 32 r and columns
 // warp + NW c, so column k lies in one warp (warp-local pivot search) and the
 // pivot row is a shared-memory broadcast.  One CTA of 32 NW threads per matrix.
-template <int RPL, int CPW, int NW>
-__global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restrict__ F, int* __restrict__ piv, int N,
+template <int RPL, int CPW, int NW, typename R, bool STAGE>
+__global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(R* __restrict__ F, int* __restrict__ piv, int N,
                                                                 long count, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char gr_raw[];
-  float* S = reinterpret_cast<float*>(gr_raw);           // N x N staging of the result
-  float* s_col = S + (size_t)N * N;                       // column k before the step
-  float* s_row = s_col + 32 * RPL;                        // pivot row before the step
+  R* S = reinterpret_cast<R*>(gr_raw);                    // N x N staging of the result (STAGE)
+  R* s_col = S + (STAGE ? (size_t)N * N : 0);             // column k before the step
+  R* s_row = s_col + 32 * RPL;                            // pivot row before the step
   int* s_used = reinterpret_cast<int*>(s_row + NW * CPW); // row already a pivot
   int* s_kinv = s_used + 32 * RPL;                        // step whose pivot row is i
   int* s_pv = s_kinv + 32 * RPL;                          // pivot row of step k
   __shared__ int s_p;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long m = blockIdx.x; m < count; m += gridDim.x) {
-    const float* G = F + m * (long)N * N;
-    float a[RPL][CPW];
+    const R* G = F + m * (long)N * N;
+    R a[RPL][CPW];
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
       const int j = w + NW * c;
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
         const int i = lane + 32 * r;
-        a[r][c] = (i < N && j < N) ? G[(long)j * N + i] : 0.0f;
+        a[r][c] = (i < N && j < N) ? G[(long)j * N + i] : (R)0;
       }
     }
     for (int i = threadIdx.x; i < 32 * RPL; i += blockDim.x) s_used[i] = (i < N) ? 0 : 1;
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
       const int wk = k % NW, ck = k / NW;
       if (w == wk) {
         // pivot search over the unused rows of column k; column k to shared memory
-        float best = -1.0f;
+        R best = (R)-1;
         int bi = 0x7fffffff;
 #pragma unroll
         for (int c = 0; c < CPW; ++c)
@@ -622,12 +622,12 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
               const int i = lane + 32 * r;
-              const float v = a[r][c];
+              const R v = a[r][c];
               s_col[i] = v;
               if (i < N && !s_used[i]) {
                 if (bi == 0x7fffffff) bi = i;  // a valid row even if every candidate is NaN
-                if (fabsf(v) > best) {
-                  best = fabsf(v);
+                if (fabs(v) > best) {
+                  best = fabs(v);
                   bi = i;
                 }
               }
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
           }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const R ov = __shfl_xor_sync(0xffffffffu, best, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ov > best || (ov == best && oi < bi)) {
             best = ov;
@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
           s_used[bi] = 1;
           s_kinv[bi] = k;
           s_pv[k] = bi;
-          if (!(best > 0.0f)) atomicExch(err, 1);
+          if (!(best > (R)0)) atomicExch(err, 1);
         }
       }
       __syncthreads();
@@ -661,8 +661,8 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
           }
       }
       __syncthreads();
-      const float inv = 1.0f / s_row[k];
-      float rj[CPW], f[RPL];
+      const R inv = (R)1 / s_row[k];
+      R rj[CPW], f[RPL];
 #pragma unroll
       for (int c = 0; c < CPW; ++c) rj[c] = s_row[w + NW * c] * inv;
 #pragma unroll
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
       if (lane == lp) {
 #pragma unroll
         for (int r = 0; r < RPL; ++r)
-          if (r == rp) f[r] = 0.0f;  // the pivot row is set below
+          if (r == rp) f[r] = (R)0;  // the pivot row is set below
       }
       if (w == wk) {
 #pragma unroll
@@ -678,13 +678,13 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
           if (c == ck) {
             rj[c] = inv;
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) a[r][c] = 0.0f;  // new column k: -a_ik / d
+            for (int r = 0; r < RPL; ++r) a[r][c] = (R)0;  // new column k: -a_ik / d
           }
       }
 #pragma unroll
       for (int r = 0; r < RPL; ++r)
 #pragma unroll
-        for (int c = 0; c < CPW; ++c) a[r][c] = fmaf(-f[r], rj[c], a[r][c]);
+        for (int c = 0; c < CPW; ++c) a[r][c] = fma(-f[r], rj[c], a[r][c]);
       if (lane == lp) {
 #pragma unroll
         for (int r = 0; r < RPL; ++r)
@@ -695,7 +695,10 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
       }
       __syncthreads();
     }
-    // (A^{-1})[s_kinv[i]][s_pv[j]] = M[i][j], staged column-major in S
+    // (A^{-1})[s_kinv[i]][s_pv[j]] = M[i][j]: staged column-major in S, or
+    // written in place (every thread has read its entries before the steps)
+    R* Go = F + m * (long)N * N;
+    R* D = STAGE ? S : Go;
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
       const int j = w + NW * c;
@@ -704,37 +707,47 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_kernel(float* __restric
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
           const int i = lane + 32 * r;
-          if (i < N) S[(long)dc * N + s_kinv[i]] = a[r][c];
+          if (i < N) D[(long)dc * N + s_kinv[i]] = a[r][c];
         }
       }
     }
     __syncthreads();
-    float* Go = F + m * (long)N * N;
-    for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) Go[t] = S[t];
+    if (STAGE)
+      for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) Go[t] = S[t];
     for (int k = threadIdx.x; k < N; k += blockDim.x) piv[m * N + k] = s_pv[k];
     __syncthreads();
   }
 }
 
-template <int RPL, int CPW>
-cudaError_t launch_gj_reg(float* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
+template <int RPL, int CPW, typename R, bool STAGE>
+cudaError_t launch_gj_reg_t(R* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
   constexpr int NW = 16;
-  const size_t sm = (size_t)N * N * sizeof(float) + (32 * RPL + NW * CPW) * sizeof(float) + 3 * 32 * RPL * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(gj_invert_reg_kernel<RPL, CPW, NW>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = (STAGE ? (size_t)N * N * sizeof(R) : 0) + (32 * RPL + NW * CPW) * sizeof(R) +
+                    3 * 32 * RPL * sizeof(int);
+  auto kern = gj_invert_reg_kernel<RPL, CPW, NW, R, STAGE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gj_invert_reg_kernel<RPL, CPW, NW>, 32 * NW, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * NW, sm);
   if (e != cudaSuccess) return e;
   const long cap = (long)(occ > 0 ? occ : 1) * nsm;
   const unsigned g = (unsigned)(count < cap ? count : cap);
-  gj_invert_reg_kernel<RPL, CPW, NW><<<g, 32 * NW, sm, st>>>(F, piv, N, count, err);
+  kern<<<g, 32 * NW, sm, st>>>(F, piv, N, count, err);
   return cudaGetLastError();
 }
 
-// FP32 patches of the sizes that occur (3D k = 0, 1; 2D k = 0..2) go to the
+// staged write-out when the N x N result fits in shared memory, else in place
+template <int RPL, int CPW, typename R>
+cudaError_t launch_gj_reg(R* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
+  if ((size_t)N * N * sizeof(R) + 8192 <= 227 * 1024)
+    return launch_gj_reg_t<RPL, CPW, R, true>(F, piv, N, count, err, nsm, st);
+  return launch_gj_reg_t<RPL, CPW, R, false>(F, piv, N, count, err, nsm, st);
+}
+
+// patches of the sizes that occur (3D k = 0, 1; 2D k = 0..2) go to the
 // register kernel; true if it was launched
-inline bool try_gj_reg(float* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st, cudaError_t& e) {
+template <typename R>
+inline bool try_gj_reg(R* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st, cudaError_t& e) {
   if (N <= 64 && N <= 16 * 4) { e = launch_gj_reg<2, 4>(F, piv, N, count, err, nsm, st); return true; }
   if (N <= 96) { e = launch_gj_reg<3, 6>(F, piv, N, count, err, nsm, st); return true; }
   if (N <= 192) { e = launch_gj_reg<6, 12>(F, piv, N, count, err, nsm, st); return true; }
@@ -1002,9 +1015,9 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
 // launch the shared-memory inversion when the matrix fits, else the global one
 template <typename T>
 cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
-  if constexpr (sizeof(T) == 4) {
+  {
     cudaError_t e = cudaSuccess;
-    if (try_gj_reg(reinterpret_cast<float*>(F), piv, N, count, err, nsm, st, e)) return e;
+    if (try_gj_reg<T>(F, piv, N, count, err, nsm, st, e)) return e;
   }
   const size_t sm = ((size_t)N * N + 2 * (size_t)N) * sizeof(T);
   int maxsm = 0, dev = 0;
