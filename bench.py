@@ -412,7 +412,7 @@ def main():
     achieved = fl / (apply_ms * 1e-3) / 1e12
     traffic, executed = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "one modN apply: st_op_kernel<3,2,double,OP_JAC,1> (all cells, colour-private outputs) + st_face_kernel (side stream) + st_node_sum", "traffic_source": os.path.relpath(PROFILE, ROOT),
+                "traffic": traffic, "kernel": "one modN apply: st_op_kernel<3,2,double,OP_JAC,1> (all cells, colour-private outputs) + st_face_kernel (side stream) + st_cbuf_sum + st_face_add", "traffic_source": os.path.relpath(PROFILE, ROOT),
                 "apply_ms": apply_ms, "flops_per_apply": fl, "flop_per_dof": FLOP_PER_DOF,
                 "executed_fp64_flops_per_apply": executed,
                 "executed_frac": (executed / (apply_ms * 1e-3) / 1e12 / peak) if executed else None,
@@ -454,9 +454,9 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d of the 32768 cells of the 32^3 mesh (element matrices formed and applied), one apply each "
                          "of Pic, exN, modN, %.1f s" % (sample, dt)}
-    # per apply: volume kernel + face kernel + node sum; per linearisation:
-    # volume + face + 2 precision casts
-    launches_per_step = len(tangents) * ((1 + 1 + 2) + APPLIES * 3)
+    # per apply: volume kernel + face kernel + class-buffer sum + face add; per
+    # linearisation: volume + face + 2 precision casts
+    launches_per_step = len(tangents) * ((1 + 1 + 2) + APPLIES * 4)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -201,12 +201,8 @@ cudaError_t build_gather(const st_problem* h, Level& L, const std::vector<int>& 
       ptr.push_back((int)ent.size());
     }
   L.n_gather = (int)node.size();
-  std::vector<int> gmap(L.Nq2 + L.Nq1, -1);  // node -> gather row (velocity nodes, then pressure nodes)
-  for (int t = 0; t < L.n_gather; ++t) gmap[(t < L.n_gather_vel ? 0 : L.Nq2) + node[t]] = t;
-  cudaError_t e = cudaMalloc(&L.d_gmap, gmap.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpy(L.d_gmap, gmap.data(), gmap.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess || node.empty()) return e;
-  e = cudaMalloc(&L.d_gnode, node.size() * sizeof(int));
+  if (node.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&L.d_gnode, node.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(L.d_gnode, node.data(), node.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&L.d_gptr, ptr.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(L.d_gptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -447,7 +443,6 @@ st_status st_destroy(st_problem* h) {
     cudaFree(L.d_gnode);
     cudaFree(L.d_gptr);
     cudaFree(L.d_gent);
-    cudaFree(L.d_gmap);
   }
   cudaFree(h->d_cbuf64);
   cudaFree(h->d_cbuf32);

@@ -13,7 +13,7 @@
 // values/normal derivatives at the 3x3 face points (tangential passes) ->
 // tangential derivatives -> pointwise face terms -> transposed passes ->
 // compact per-slot output (values and normal-derivative weights at the face
-// nodes, pressure tests) in a scratch array.  st_node_sum then adds these
+// nodes, pressure tests) in a scratch array.  st_face_add then adds these
 // into the output per global node, after the volume kernel.
 #pragma once
 
@@ -443,76 +443,61 @@ struct GatherEnt {
   double ed;  // weight of the face normal-derivative output
 };
 
-// out = sum of the 2^DIM class-private volume outputs (entries a class does
-// not reach are zero in its buffer, so every class is added, in a fixed
-// order) + the boundary-face contributions of the face scratch (CSR row of
-// the node, if any).  One thread per spatial node: a velocity node handles
-// its K1 x DIM slab entries, a pressure node its K1 entries, so the gather
-// lists are read once per node and all class loads of a thread are
-// independent.  Writes every entry of out.
+// out = sum of the 2^DIM class-private volume outputs, fixed class order,
+// two entries per thread (16-byte loads when the slab length allows it).
+template <int DIM, typename T>
+__global__ void st_cbuf_sum(const T* __restrict__ cb, long stride, long n, T* __restrict__ out) {
+  constexpr int NCOL = 1 << DIM;
+  const long n2 = (stride % 2 == 0) ? n / 2 : 0;  // pairs (aligned when the stride is even)
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += (long)gridDim.x * blockDim.x) {
+    T a0 = cb[2 * t], a1 = cb[2 * t + 1];
+#pragma unroll
+    for (int c = 1; c < NCOL; ++c) {
+      a0 += cb[c * stride + 2 * t];
+      a1 += cb[c * stride + 2 * t + 1];
+    }
+    out[2 * t] = a0;
+    out[2 * t + 1] = a1;
+  }
+  for (long i = 2 * n2 + (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    T a = cb[i];
+#pragma unroll
+    for (int c = 1; c < NCOL; ++c) a += cb[c * stride + i];
+    out[i] = a;
+  }
+}
+
+// out += the boundary-face contributions of the face scratch: one thread per
+// (gather row, Radau node, component) of the boundary-cell layer.
 template <int DIM, int K1, typename T>
-__global__ void st_node_sum(const OpArgs a, const int* __restrict__ gmap, const int* __restrict__ gptr,
-                            const GatherEnt* __restrict__ gent, const T* __restrict__ fscr, T* __restrict__ out) {
+__global__ void st_face_add(const OpArgs a, int nvel, int ntot, const int* __restrict__ gnode,
+                            const int* __restrict__ gptr, const GatherEnt* __restrict__ gent,
+                            const T* __restrict__ fscr, T* __restrict__ out) {
   using D = Dims<DIM>;
-  constexpr int NC = D::NC, NFQ = D::NFQ, NCOL = 1 << DIM;
+  constexpr int NC = D::NC, NFQ = D::NFQ;
   constexpr int NOUT = 2 * NC * NFQ + D::NFP;
-  const T* cb = reinterpret_cast<const T*>(a.cbuf);
-  const int nq2 = (int)a.Nq2, nq1 = (int)a.Nq1, mv = (int)a.Mv, mp = (int)a.Mp;
-  const long cs = a.cbuf_stride;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq2 + nq1; t += gridDim.x * blockDim.x) {
-    if (t < nq2) {
-      const int g = t;
-      T acc[K1 * NC];
-#pragma unroll
-      for (int mu = 0; mu < K1; ++mu)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const long e = (long)mu * mv + (long)c * nq2 + g;
-          T v = cb[e];
-#pragma unroll
-          for (int col = 1; col < NCOL; ++col) v += cb[col * cs + e];
-          acc[mu * NC + c] = v;
-        }
-      const int row = gmap[g];
-      if (row >= 0) {
-        const int b = gptr[row], e = gptr[row + 1];
-        for (int j = b; j < e; ++j) {
-          const GatherEnt ge = gent[j];
-          const T ev = (T)ge.e, ed = (T)ge.ed;
-#pragma unroll
-          for (int mu = 0; mu < K1; ++mu) {
-            const T* fs = fscr + ((long)ge.fid * K1 + mu) * NOUT + ge.tn;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) acc[mu * NC + c] += ev * fs[c * NFQ] + ed * fs[NC * NFQ + c * NFQ];
-          }
-        }
+  const long nv = (long)nvel * K1 * NC, np = (long)(ntot - nvel) * K1;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nv + np; t += (long)gridDim.x * blockDim.x) {
+    if (t < nv) {
+      const int row = (int)(t / (K1 * NC)), mc = (int)(t % (K1 * NC)), mu = mc / NC, c = mc % NC;
+      const int b = gptr[row], e = gptr[row + 1];
+      T acc = 0;
+      for (int j = b; j < e; ++j) {
+        const GatherEnt ge = gent[j];
+        const T* fs = fscr + ((long)ge.fid * K1 + mu) * NOUT + ge.tn + c * NFQ;
+        acc += (T)ge.e * fs[0] + (T)ge.ed * fs[NC * NFQ];
       }
-#pragma unroll
-      for (int mu = 0; mu < K1; ++mu)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) out[(long)mu * mv + (long)c * nq2 + g] = acc[mu * NC + c];
+      out[(long)mu * a.Mv + (long)c * a.Nq2 + gnode[row]] += acc;
     } else {
-      const int g = t - nq2;
-      T acc[K1];
-#pragma unroll
-      for (int mu = 0; mu < K1; ++mu) {
-        const long e = (long)K1 * mv + (long)mu * mp + g;
-        T v = cb[e];
-#pragma unroll
-        for (int col = 1; col < NCOL; ++col) v += cb[col * cs + e];
-        acc[mu] = v;
+      const long u = t - nv;
+      const int row = nvel + (int)(u / K1), mu = (int)(u % K1);
+      const int b = gptr[row], e = gptr[row + 1];
+      T acc = 0;
+      for (int j = b; j < e; ++j) {
+        const GatherEnt ge = gent[j];
+        acc += fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
       }
-      const int row = gmap[nq2 + g];
-      if (row >= 0) {
-        const int b = gptr[row], e = gptr[row + 1];
-        for (int j = b; j < e; ++j) {
-          const GatherEnt ge = gent[j];
-#pragma unroll
-          for (int mu = 0; mu < K1; ++mu) acc[mu] += fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
-        }
-      }
-#pragma unroll
-      for (int mu = 0; mu < K1; ++mu) out[(long)K1 * mv + (long)mu * mp + g] = acc[mu];
+      out[(long)K1 * a.Mv + (long)mu * a.Mp + gnode[row]] += acc;
     }
   }
 }

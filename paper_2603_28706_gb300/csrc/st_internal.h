@@ -139,7 +139,6 @@ struct Level {
   int* d_gnode = nullptr;
   int* d_gptr = nullptr;
   void* d_gent = nullptr;
-  int* d_gmap = nullptr;       // Nq2 + Nq1: gather row of every velocity / pressure node, -1 off the boundary layer
   // Vanka / coarse operator storage (set up by the preconditioner)
 };
 

@@ -35,15 +35,24 @@ cudaError_t launch_faces_t(const st_problem* h, const Level& L, const OpArgs& a,
   return cudaGetLastError();
 }
 
-// out = sum of the class buffers + face contributions (one thread per node)
+// out = sum of the class buffers (streaming), then += the face
+// contributions of the boundary-cell layer
 template <int DIM, int K1, typename T>
 cudaError_t launch_node_sum_t(const st_problem* h, const Level& L, const OpArgs& a, cudaStream_t st) {
-  long g = (L.Nq2 + L.Nq1 + 255) / 256;
+  long g = (L.Nst / 2 + 255) / 256;
   if (g > 16L * h->nsm) g = 16L * h->nsm;
-  st_node_sum<DIM, K1, T><<<(unsigned)g, 256, 0, st>>>(a, L.d_gmap, L.d_gptr,
-                                                       reinterpret_cast<const GatherEnt*>(L.d_gent),
-                                                       reinterpret_cast<const T*>(h->d_fscr),
-                                                       reinterpret_cast<T*>(a.out));
+  if (g < 1) g = 1;
+  st_cbuf_sum<DIM, T><<<(unsigned)g, 256, 0, st>>>(reinterpret_cast<const T*>(a.cbuf), a.cbuf_stride, L.Nst,
+                                                    reinterpret_cast<T*>(a.out));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || L.n_gather == 0) return e;
+  const long items = (long)L.n_gather_vel * K1 * DIM + (long)(L.n_gather - L.n_gather_vel) * K1;
+  long gf = (items + 255) / 256;
+  if (gf > 16L * h->nsm) gf = 16L * h->nsm;
+  st_face_add<DIM, K1, T><<<(unsigned)gf, 256, 0, st>>>(a, L.n_gather_vel, L.n_gather, L.d_gnode, L.d_gptr,
+                                                        reinterpret_cast<const GatherEnt*>(L.d_gent),
+                                                        reinterpret_cast<const T*>(h->d_fscr),
+                                                        reinterpret_cast<T*>(a.out));
   return cudaGetLastError();
 }
 
@@ -67,7 +76,7 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   // scratch (or, when linearising, the face cache).  The volume kernel (one
   // launch over all cells in colour order) writes every cell's contributions
   // into the private buffer of its colour class with plain stores.  The
-  // caller's stream then waits for the face kernel and st_node_sum forms
+  // caller's stream then waits for the face kernel; st_cbuf_sum and st_face_add form
   // out = sum of the class buffers + face contributions, one thread per node.
   cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);

@@ -678,7 +678,7 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
         }
         // plain stores into the private buffer of the cell's colour class:
         // cells of one class share no node, so no two threads write the same
-        // entry; st_node_sum adds the classes' buffers afterwards
+        // entry; st_cbuf_sum adds the classes' buffers afterwards
         T* ob = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)mu * a.Mv +
                 c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
 #pragma unroll
