@@ -104,3 +104,24 @@ def test_vcycle(case):
             d = prob.vcycle(dev(r, dt), prec=prec)
             assert rel(d, ref) <= tol, (tg, prec, rel(d, ref))
         prob.close()
+
+
+def test_vcycle_graph_replay_is_bitwise_equal():
+    # the first call with a buffer pair runs eagerly, the second is captured
+    # as a CUDA graph, the third replays it: all three give the same bits
+    p = si.base_params(dim=3, nx=4, ny=4, nz=4, k=1, p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05,
+                       levels=2, coarse_sweeps=4)
+    st = gpu()
+    U = smooth_state(p)
+    s = oracle.sizes(p)
+    prob = st.Problem(p)
+    prob.linearize(2, dev(U))
+    for prec, dt in ((st.ST_FP32, torch.float32), (st.ST_FP64, torch.float64)):
+        r = dev(si.uniform(s["Nst"], 5), dt)
+        d = torch.empty_like(r)
+        outs = []
+        for _ in range(3):
+            prob.vcycle(r, d, prec=prec)
+            outs.append(d.clone())
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2]), prec
+    prob.close()
