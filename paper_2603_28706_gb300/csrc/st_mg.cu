@@ -100,77 +100,6 @@ __global__ void restrict_pass(const T* __restrict__ x, T* __restrict__ y, int gi
 // E_c[cell][mu] = sum over the 2^d children of P_ch^T E_f[child][mu] P_ch, with
 // P_ch the child-local-dof <- parent-local-dof prolongation (block diagonal:
 // one tensor Q2 block per velocity component, one Q1 block for the pressure).
-struct TransferTabs {
-  double P2[15], P1[6];
-};
-
-double pch(int DIM, const TransferTabs& tt, int j, int b, const int off[3]) {
-  // j: child-local dof, b: parent-local dof
-  const int NQ = DIM == 3 ? 27 : 9, NC = DIM;
-  const bool vj = j < NC * NQ, vb = b < NC * NQ;
-  if (vj != vb) return 0.0;
-  if (vj) {
-    if (j / NQ != b / NQ) return 0.0;
-    const int n = j % NQ, m = b % NQ;
-    const int ni[3] = {n % 3, (n / 3) % 3, n / 9}, mi[3] = {m % 3, (m / 3) % 3, m / 9};
-    double v = 1.0;
-    for (int d = 0; d < DIM; ++d) v *= tt.P2[(2 * off[d] + ni[d]) * 3 + mi[d]];
-    return v;
-  }
-  const int n = j - NC * NQ, m = b - NC * NQ;
-  const int ni[3] = {n & 1, (n >> 1) & 1, n >> 2}, mi[3] = {m & 1, (m >> 1) & 1, m >> 2};
-  double v = 1.0;
-  for (int d = 0; d < DIM; ++d) v *= tt.P1[(off[d] + ni[d]) * 2 + mi[d]];
-  return v;
-}
-
-template <int DIM, typename T>
-__global__ void galerkin_kernel(const T* __restrict__ Ef, T* __restrict__ Ec, int ncx, int ncy, int ncz, int K1,
-                                const double* __restrict__ Pch) {
-  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NE = NC * NQ + (DIM == 3 ? 8 : 4);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sE = reinterpret_cast<T*>(smraw);  // child matrix
-  T* sT = sE + NE * NE;                  // E_f P
-  T* sR = sT + NE * NE;                  // result
-  const long ncell = (long)ncx * ncy * ncz;
-  const int nfx = 2 * ncx, nfy = 2 * ncy;
-  for (long item = blockIdx.x; item < ncell * K1; item += gridDim.x) {
-    const long cc = item / K1;
-    const int mu = (int)(item % K1);
-    const int cx = (int)(cc % ncx), cy = (int)((cc / ncx) % ncy), cz = (int)(cc / ((long)ncx * ncy));
-    for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) sR[i] = 0;
-    for (int ch = 0; ch < (1 << DIM); ++ch) {
-      const int off[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-      const long fcell = (2 * cx + off[0]) + (long)nfx * ((2 * cy + off[1]) + (long)nfy * (DIM == 3 ? 2 * cz + off[2] : 0));
-      const T* src = Ef + (fcell * K1 + mu) * NE * NE;
-      const double* sP = Pch + (long)ch * NE * NE;
-      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) sE[i] = src[i];
-      __syncthreads();
-      // T = E_f P (P block diagonal: only same-block columns contribute)
-      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) {
-        const int r = i / NE, b = i % NE;
-        const int j0 = b < NC * NQ ? (b / NQ) * NQ : NC * NQ, j1 = b < NC * NQ ? j0 + NQ : NE;
-        T acc = 0;
-        for (int j = j0; j < j1; ++j) acc += sE[r * NE + j] * (T)sP[j * NE + b];
-        sT[i] = acc;
-      }
-      __syncthreads();
-      // R += P^T T
-      for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) {
-        const int aa = i / NE, b = i % NE;
-        const int j0 = aa < NC * NQ ? (aa / NQ) * NQ : NC * NQ, j1 = aa < NC * NQ ? j0 + NQ : NE;
-        T acc = 0;
-        for (int j = j0; j < j1; ++j) acc += (T)sP[j * NE + aa] * sT[j * NE + b];
-        sR[i] += acc;
-      }
-      __syncthreads();
-    }
-    T* dst = Ec + (cc * K1 + mu) * NE * NE;
-    for (int i = threadIdx.x; i < NE * NE; i += blockDim.x) dst[i] = sR[i];
-    __syncthreads();
-  }
-}
-
 // Sum-factorised Galerkin coarsening.  The child prolongation is block
 // diagonal with Kronecker blocks: per velocity component P2[oz] (x) P2[oy]
 // (x) P2[ox] (3x3 1D blocks, rows child node, columns parent node), for the
@@ -478,98 +407,6 @@ __global__ void gj_invert_kernel(T* __restrict__ F, int* __restrict__ piv, int N
         }
       __syncthreads();
     }
-  }
-}
-
-// The same inversion with the matrix resident in shared memory (it must fit:
-// N^2 elements): one CTA of JG x RP threads per matrix, RP = N rounded up to a
-// warp multiple; thread (jg, i) owns row i of the columns j = jg (mod JG) in
-// the elimination, so its multiplier stays in a register and the pivot-row
-// entry is a shared-memory broadcast.
-template <typename T>
-__global__ void gj_invert_smem_kernel(T* __restrict__ F, int* __restrict__ piv, int N, long count,
-                                      int* __restrict__ err) {
-  extern __shared__ __align__(16) unsigned char gj_raw[];
-  T* A = reinterpret_cast<T*>(gj_raw);          // N x N, column-major
-  T* s_row = A + (size_t)N * N;                 // scaled pivot row
-  T* s_col = s_row + N;                         // multipliers (column k)
-  __shared__ T w_val[32];
-  __shared__ int w_idx[32];
-  __shared__ int s_piv;
-  const int RP = (N + 31) & ~31, JG = blockDim.x / RP;
-  const int i = threadIdx.x % RP, jg = threadIdx.x / RP;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (long m = blockIdx.x; m < count; m += gridDim.x) {
-    T* G = F + m * (long)N * N;
-    int* pv = piv + m * N;
-    for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) A[t] = G[t];
-    __syncthreads();
-    for (int k = 0; k < N; ++k) {
-      // pivot search by the jg == 0 threads (warps 0 .. RP/32-1)
-      if (jg == 0) {
-        T v = (i >= k && i < N) ? fabs(A[(long)k * N + i]) : (T)-1;
-        int vi = i;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const T ov = __shfl_down_sync(0xffffffffu, v, o);
-          const int oi = __shfl_down_sync(0xffffffffu, vi, o);
-          if (ov > v || (ov == v && oi < vi)) {
-            v = ov;
-            vi = oi;
-          }
-        }
-        if (lane == 0) {
-          w_val[warp] = v;
-          w_idx[warp] = vi;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        T v = w_val[0];
-        int vi = w_idx[0];
-        for (int w = 1; w < RP / 32; ++w)
-          if (w_val[w] > v || (w_val[w] == v && w_idx[w] < vi)) {
-            v = w_val[w];
-            vi = w_idx[w];
-          }
-        s_piv = vi;
-        pv[k] = vi;
-        if (!(v > 0)) atomicExch(err, 1);
-      }
-      __syncthreads();
-      const int p = s_piv;
-      const T d = A[(long)k * N + p];
-      const T inv = d != (T)0 ? (T)1 / d : (T)0;
-      for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const T rk = A[(long)j * N + p];
-        if (p != k) A[(long)j * N + p] = A[(long)j * N + k];
-        s_row[j] = (j == k ? (T)1 : rk) * inv;
-      }
-      __syncthreads();
-      for (int r = threadIdx.x; r < N; r += blockDim.x) s_col[r] = (r == k) ? (T)0 : A[(long)k * N + r];
-      __syncthreads();
-      if (i < N) {
-        const T f = s_col[i];
-        for (int j = jg; j < N; j += JG) {
-          T* aij = A + (long)j * N + i;
-          if (i == k) *aij = s_row[j];
-          else *aij = (j == k ? (T)0 : *aij) - f * s_row[j];
-        }
-      }
-      __syncthreads();
-    }
-    for (int k = N - 1; k >= 0; --k) {
-      const int p = pv[k];
-      if (p != k)
-        for (int r = threadIdx.x; r < N; r += blockDim.x) {
-          const T t = A[(long)k * N + r];
-          A[(long)k * N + r] = A[(long)p * N + r];
-          A[(long)p * N + r] = t;
-        }
-      __syncthreads();
-    }
-    for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) G[t] = A[t];
-    __syncthreads();
   }
 }
 
@@ -1012,33 +849,14 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
   }
 }
 
-// launch the shared-memory inversion when the matrix fits, else the global one
+// the register kernel when the patch size allows it, else the global-memory one
 template <typename T>
 cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm, cudaStream_t st) {
-  {
-    cudaError_t e = cudaSuccess;
-    if (try_gj_reg<T>(F, piv, N, count, err, nsm, st, e)) return e;
-  }
-  const size_t sm = ((size_t)N * N + 2 * (size_t)N) * sizeof(T);
-  int maxsm = 0, dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  if (sm + 1024 <= (size_t)maxsm) {
-    const int RP = (N + 31) & ~31;
-    const int JG = RP <= 128 ? 4 : (RP <= 512 ? 2 : 1);
-    e = cudaFuncSetAttribute(gj_invert_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    int occ = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gj_invert_smem_kernel<T>, JG * RP, sm);
-    if (e != cudaSuccess) return e;
-    const long cap = (long)(occ > 0 ? occ : 1) * nsm;
-    const unsigned g = (unsigned)(count < cap ? count : cap);
-    gj_invert_smem_kernel<T><<<g, JG * RP, sm, st>>>(F, piv, N, count, err);
-  } else {
-    const unsigned g = (unsigned)(count < 8L * nsm ? count : 8L * nsm);
-    gj_invert_kernel<T><<<g, 256, 0, st>>>(F, piv, N, count, err);
-  }
+  cudaError_t e = cudaSuccess;
+  if (try_gj_reg<T>(F, piv, N, count, err, nsm, st, e)) return e;
+  // larger patches (3D, k >= 2): the global-memory kernel
+  const unsigned g = (unsigned)(count < 8L * nsm ? count : 8L * nsm);
+  gj_invert_kernel<T><<<g, 256, 0, st>>>(F, piv, N, count, err);
   return cudaGetLastError();
 }
 
@@ -1218,7 +1036,6 @@ struct MgState {
   int* bcells = nullptr;         // boundary cells (linear) of the finest level
   int nbc = 0;
   double* d_tab = nullptr;       // 1D transfer tables on the device (P2, P1)
-  double* d_pch = nullptr;       // child <- parent local prolongation matrices [2^d][NE][NE]
   // the V-cycle as a CUDA graph, for the (r, d, precision, tangent) it was captured with
   cudaGraphExec_t gexec = nullptr;
   const void* g_r = nullptr;
@@ -1265,8 +1082,6 @@ void free_mg(MgState* m) {
   cudaFree(m->fcache_rep32);
   cudaFree(m->bcells);
   cudaFree(m->d_tab);
-  cudaFree(m->d_pch);
-  m->d_pch = nullptr;
   m->Erep = nullptr;
   m->Urep = nullptr;
   m->cache_rep64 = m->fcache_rep64 = nullptr;
@@ -1326,20 +1141,6 @@ cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
     memcpy(tab + 15, h->R.P1, sizeof(h->R.P1));
     e = cudaMalloc(&m->d_tab, sizeof(tab));
     if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
-  }
-  if (e == cudaSuccess) {
-    TransferTabs tt;
-    memcpy(tt.P2, h->R.P2, sizeof(tt.P2));
-    memcpy(tt.P1, h->R.P1, sizeof(tt.P1));
-    const int nch = 1 << h->dim;
-    std::vector<double> P((size_t)nch * NE * NE);
-    for (int ch = 0; ch < nch; ++ch) {
-      const int off[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
-      for (int j = 0; j < NE; ++j)
-        for (int b = 0; b < NE; ++b) P[((size_t)ch * NE + j) * NE + b] = pch(h->dim, tt, j, b, off);
-    }
-    e = cudaMalloc(&m->d_pch, P.size() * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_pch, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
   m->prec = prec;
   m->allocated = e == cudaSuccess;
