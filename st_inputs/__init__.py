@@ -5,8 +5,10 @@ smooth random velocity fields sampled at nodes).  It holds none of the
 method's arithmetic: no basis functions, quadrature, residual or Jacobian.
 
 Parameter dictionaries carry the fields of both the oracle's and the
-library's parameter structs.  Readings where the workloads leave a value open
-(viscosities, boundary split, penalties) are documented in the design doc.
+library's parameter structs.  Where a workload leaves a value open the
+defaults below fix it: nu = 1e-3 and nu_inf = 1e-4 for the 3D workloads, the
+do-nothing boundary at x = x_max with Nitsche Dirichlet data elsewhere, and
+the Nitsche penalties gamma1 = gamma2 = 1e3.
 """
 import math
 

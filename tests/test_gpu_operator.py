@@ -1,7 +1,7 @@
 """Parity of the CUDA slab operator (residual, linearisation + Jacobian action
 for Pic / exN / modN) with the FP64 oracle, through the C ABI.
 
-Tolerances (spec bar): FP64 max|gpu - oracle| <= 1e-12 max|oracle|,
+Tolerances: FP64 max|gpu - oracle| <= 1e-12 max|oracle|,
 FP32 <= 1e-5 max|oracle|, element by element over the whole vector."""
 import numpy as np
 import pytest
