@@ -824,19 +824,31 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
       ss[b][q][1] = im;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nb * NE; t += blockDim.x) {
-      const int b = t / NE, p = t % NE;
+    // two threads (adjacent lanes) per output row, each over every other
+    // column; the loop runs over whole warps (blockDim is a multiple of 32) so
+    // that every lane takes part in the pair shuffle
+    const int total = 2 * nb * NE, padded = (total + 31) & ~31;
+    for (int t = threadIdx.x; t < padded; t += blockDim.x) {
+      const bool act = t < total;
+      const int row = act ? t >> 1 : 0, half = t & 1;
+      const int b = row / NE, p = row % NE;
       const T* gb = Gk + (long)b * NE * NE * 2 + 2 * p;
       T re = 0, im = 0;
+      if (act) {
 #pragma unroll 4
-      for (int q = 0; q < NE; ++q) {
-        const T gr = gb[(long)q * NE * 2], gi = gb[(long)q * NE * 2 + 1];
-        const T sr = ss[b][q][0], si = ss[b][q][1];
-        re = fma(gr, sr, fma(-gi, si, re));
-        im = fma(gr, si, fma(gi, sr, im));
+        for (int q = half; q < NE; q += 2) {
+          const T gr = gb[(long)q * NE * 2], gi = gb[(long)q * NE * 2 + 1];
+          const T sr = ss[b][q][0], si = ss[b][q][1];
+          re = fma(gr, sr, fma(-gi, si, re));
+          im = fma(gr, si, fma(gi, sr, im));
+        }
       }
-      sz[b][p][0] = re;
-      sz[b][p][1] = im;
+      re += __shfl_xor_sync(0xffffffffu, re, 1);
+      im += __shfl_xor_sync(0xffffffffu, im, 1);
+      if (act && half == 0) {
+        sz[b][p][0] = re;
+        sz[b][p][1] = im;
+      }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
