@@ -243,6 +243,15 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NE = NC * NQ + (DIM == 3 ? 8 : 4);
   const int K1 = pa.K1, N = K1 * NE;
   const long ncell = (long)pa.n[0] * pa.n[1] * (DIM == 3 ? pa.n[2] : 1);
+  __shared__ double smass[NQ * NQ];  // element velocity mass (tensor of the 1D masses)
+  for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) {
+    const int a = t / NQ, b = t % NQ;
+    const int ai[3] = {a % 3, (a / 3) % 3, a / 9}, bi[3] = {b % 3, (b / 3) % 3, b / 9};
+    double m = 1.0;
+    for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
+    smass[t] = m;
+  }
+  __syncthreads();
   for (long K = blockIdx.x; K < ncell; K += gridDim.x) {
     const int k3[3] = {(int)(K % pa.n[0]), (int)((K / pa.n[0]) % pa.n[1]),
                        DIM == 3 ? (int)(K / ((long)pa.n[0] * pa.n[1])) : 0};
@@ -270,13 +279,7 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
             } else {
               for (int mu = 0; mu < K1; ++mu) S[mu] += E[(ecell * estride + mu) * NE * NE + (long)lp * NE + lq];
             }
-            if (vel_pair) {
-              const int a = lp % NQ, b = lq % NQ;
-              const int ai[3] = {a % 3, (a / 3) % 3, a / 9}, bi[3] = {b % 3, (b / 3) % 3, b / 9};
-              double m = 1.0;
-              for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
-              mass += m;
-            }
+            if (vel_pair) mass += smass[(lp % NQ) * NQ + (lq % NQ)];
           }
       if (pa.c13) {
         // block b: lambda_b M_v + S_0 (S_0: the surrogate block of node 0), complex, column-major
