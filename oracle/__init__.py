@@ -15,6 +15,9 @@ Functions and the passages they follow:
                      tangents of eq. local-tangent-picard/-exact/-clip
   st_element_matrices, spatial_element_matrices, assemble_csr
                      the same operator as element matrices / assembled CSR
+  cip_csr            the CIP term of eq. scip-def (lagged weight) assembled
+                     from its face blocks; residual and jacobian_apply include
+                     it when p["gamma_cip"] > 0
   mnorm2             block mass-weighted norm of Sec. 6.1
   pointwise          S(A), DS(A)(B), the three tangents (Sec. 2, 4.2-4.4)
   time_tables        right Gauss-Radau nodes/weights, K_t, m_t, M_t (Sec. 5.2)
@@ -55,7 +58,7 @@ class OrParams(ctypes.Structure):
                 ("nu_inf", ctypes.c_double), ("sigma_max", ctypes.c_double),
                 ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
                 ("dirichlet_mask", ctypes.c_uint), ("inflow_profile", ctypes.c_int),
-                ("vbar", ctypes.c_double), ("q_sign", ctypes.c_double)]
+                ("vbar", ctypes.c_double), ("q_sign", ctypes.c_double), ("gamma_cip", ctypes.c_double)]
 
 
 _lib = None
@@ -83,12 +86,13 @@ def lib():
         _lib.or_cell_spatial_dofs.argtypes = [P, ctypes.c_long, L, L]
         _lib.or_time_tables.argtypes = [ctypes.c_int, d, d, d, d, d]
         _lib.or_gauss01.argtypes = [ctypes.c_int, d, d]
+        _lib.or_cip_blocks.argtypes = [P, d, L, L, d]
     return _lib
 
 
 def params(p):
     """OrParams from a parameter dict (see st_inputs.base_params)."""
-    return OrParams(*[p[name] for name, _ in OrParams._fields_])
+    return OrParams(*[p.get(name, 0.0) if name == "gamma_cip" else p[name] for name, _ in OrParams._fields_])
 
 
 def _d(a):
@@ -222,8 +226,9 @@ def pointwise(p, which, var, A, B=None):
     return out[0] if which == 3 else out.reshape(3, 3)
 
 
-def assemble_csr(p, var, U, mask=T_ALL, with_time=True, gnod=None):
-    """Assembled space-time Jacobian J_n(U) (scipy CSR) from element matrices."""
+def assemble_csr(p, var, U, mask=T_ALL, with_time=True, gnod=None, cip=True):
+    """Assembled space-time Jacobian J_n(U) (scipy CSR) from element matrices,
+    plus the CIP matrix when p["gamma_cip"] > 0 and cip is set."""
     import scipy.sparse as sp
     s = sizes(p)
     cells = np.arange(s["ncells"])
@@ -232,7 +237,27 @@ def assemble_csr(p, var, U, mask=T_ALL, with_time=True, gnod=None):
     N = D.shape[1]
     rows = np.repeat(D, N, axis=1).reshape(-1)
     cols = np.tile(D, (1, N)).reshape(-1)
-    return sp.csr_matrix((E.reshape(-1), (rows, cols)), shape=(s["Nst"], s["Nst"]))
+    A = sp.csr_matrix((E.reshape(-1), (rows, cols)), shape=(s["Nst"], s["Nst"]))
+    if cip and p.get("gamma_cip", 0.0) > 0.0:
+        A = (A + cip_csr(p, U)).tocsr()
+    return A
+
+
+def cip_csr(p, U):
+    """CIP matrix of the slab, eq. scip-def at every Radau node weighted by
+    tau w_mu, with the advecting field lagged at U (scipy CSR)."""
+    import scipy.sparse as sp
+    s = sizes(p)
+    d = p["dim"]
+    nl = 27 if d == 3 else 9
+    nblk = s["ncells"] * 2 * d * (p["k"] + 1) * d
+    rows = np.zeros((nblk, nl), dtype=np.int64)
+    cols = np.zeros((nblk, 2 * nl), dtype=np.int64)
+    vals = np.zeros((nblk, nl, 2 * nl))
+    lib().or_cip_blocks(ctypes.byref(params(p)), _d(_f64(U)), _l(rows), _l(cols), _d(vals))
+    r = np.repeat(rows, 2 * nl, axis=1).reshape(-1)
+    c = np.tile(cols, (1, nl)).reshape(-1)
+    return sp.csr_matrix((vals.reshape(-1), (r, c)), shape=(s["Nst"], s["Nst"]))
 
 
 def spatial_csr(p, var, u, mask=T_ALL, gnod=None):

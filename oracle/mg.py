@@ -20,7 +20,10 @@ restatement on the oracle's assembled matrices, small meshes only:
                      treatment, prolongation, post-smoothing
 Readings (the paper defers to its references here): the coarsest level is
 treated by `coarse_sweeps` additive Vanka steps with exact patches starting
-from zero; patches are cell patches; omega is a scalar.
+from zero; patches are cell patches; omega is a scalar.  With CIP (eq.
+scip-def) the finest-level defects use the full Jacobian, while the patch
+matrices and the Galerkin coarse operators are built from its cell-local part
+(everything but the interior-face CIP coupling).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -111,7 +114,7 @@ def rep_state(p, U):
 
 def surrogate_operator(p, var, U):
     """Global operator whose cell patches are the surrogate patches of eq. surrogate-diag."""
-    return assemble_csr(p, var, rep_state(p, U))
+    return assemble_csr(p, var, rep_state(p, U), cip=False)
 
 
 class Hierarchy:
@@ -133,12 +136,15 @@ class Hierarchy:
             self.P[l] = prolongation(self.params[l - 1])
         self.dofs = [cell_dofs(pl, np.arange(sizes(pl)["ncells"])) for pl in self.params]
         self.A = [None] * levels
+        self.Afine = None  # finest-level operator of the defects (with CIP)
         self.Ainv = [None] * levels
         self.update(var, U, rebuild_finest=True)
 
     def update(self, var, U, rebuild_finest):
         L = self.levels - 1
-        self.A[L] = assemble_csr(self.p, var, U)
+        self.A[L] = assemble_csr(self.p, var, U, cip=False)
+        cip = self.p.get("gamma_cip", 0.0) > 0.0
+        self.Afine = assemble_csr(self.p, var, U) if cip else self.A[L]
         for l in range(L, 0, -1):
             self.A[l - 1] = galerkin(self.A[l], self.P[l])
         for l in range(self.levels):
@@ -147,8 +153,11 @@ class Hierarchy:
             src = surrogate_operator(self.p, var, U) if (l == L and self.surrogate) else self.A[l]
             self.Ainv[l] = [np.linalg.inv(exact_patch(src, dof)) for dof in self.dofs[l]]
 
+    def op(self, l):
+        return self.Afine if l == self.levels - 1 else self.A[l]
+
     def vanka_step(self, l, r, d):
-        A = self.A[l]
+        A = self.op(l)
         defect = r - A @ d
         corr = np.zeros_like(d)
         for c, dof in enumerate(self.dofs[l]):
@@ -167,6 +176,6 @@ class Hierarchy:
         if l == 0:
             return self.smooth(0, r, d, self.coarse_sweeps)
         d = self.smooth(l, r, d, self.pre)
-        rc = self.P[l].T @ (r - self.A[l] @ d)
+        rc = self.P[l].T @ (r - self.op(l) @ d)
         d = d + self.P[l] @ self.vcycle(rc, l - 1)
         return self.smooth(l, r, d, self.post)

@@ -25,7 +25,10 @@
 //   * Nitsche terms B_gamma = B^c + B^s + B^r_gamma (eq. def-b-gam) with the
 //     viscous coefficients frozen at the lifting g_hat (Sec. 3.2); the sign of
 //     the (u.n, q) term in B^s is the parameter q_sign (-1 = the printed text);
-//   * h_GammaD = cell edge length normal to the face; CIP is not included.
+//   * h_GammaD = cell edge length normal to the face;
+//   * CIP (eq. scip-def, weight gamma_cip; 0 = off) on the interior faces,
+//     its advecting field lagged in the Jacobian (Sec. 4.3); h_F = the
+//     diameter (diagonal) of the face.
 //
 // Unknown layout: U = [V_1 .. V_{k+1} | P_1 .. P_{k+1}], V_mu component-major,
 // each component lexicographic (x fastest) on the Q2 node grid
@@ -54,6 +57,7 @@ struct OrParams {
   int inflow_profile;       // 0: g_D = 0; 1: parabolic x-inflow, lifting constant in x
   double vbar;
   double q_sign;            // coefficient of (u.n, q)_{Gamma_D} in B^s
+  double gamma_cip;         // CIP weight gamma_CIP of eq. scip-def (0: no CIP)
 };
 }
 
@@ -862,6 +866,62 @@ void cell_st_matrix(const Ctx& C, long cell, int var, const double* U, const dou
             Jst[(long)(mu * ne + comp * nl + a) * N + nu * ne + comp * nl + b] += C.T.Kt[mu][nu] * Me[a * nl + b];
 }
 
+// ------------------------------------------------------------------- CIP
+// Convection-aligned CIP term of eq. scip-def on the interior faces F:
+//   s(uhat; u, v) = sum_F gamma_cip h_F^2 (|uhat.n_F| [d_n u], [d_n v])_F,
+// d_n = derivative along n_F = e_a for the faces normal to axis a, [w] = w on
+// the upper cell minus w on the lower cell, h_F the diameter of F (its
+// diagonal), 3-point Gauss quadrature per tangential direction.  In the slab
+// forms the term is taken at every Radau node with the weight tau w_mu of M_t.
+// It is evaluated cell by cell: the jump of the test function is the
+// difference of its two one-sided traces, so cell K adds
+//   sign_K * weight * [d_n u] * d_n phi_i|K     (sign_K = +1 if K is the
+// upper cell of F, -1 if it is the lower one)
+// to its own test functions phi_i; the sum over the cells is the face sum.
+// Rloc[mu*ne + i] += scale * (that), for u = X; the weight |uhat.n_F| is taken
+// from the real field Uhat (the lagged advecting field).
+template <class S>
+void cell_cip(const Ctx& C, long cell, const S* X, const double* Uhat, double scale, S* Rloc) {
+  const Geo& G = C.G;
+  const OrParams& P = C.P;
+  const int K1 = G.k + 1, nl = G.nv / G.d, ne = G.ne;
+  const long cstride[3] = {1, (long)G.n[0], (long)G.n[0] * G.n[1]};
+  CellPos cp = cell_pos(G, cell);
+  long so[128], sn[128];
+  cell_spatial_dofs(G, cell, so);
+  for (int side = 0; side < 2 * G.d; ++side) {
+    if (on_side(G, cp, side)) continue;  // boundary faces are not in the interior skeleton
+    const int a = side / 2, up = side % 2;
+    const long nb = up ? cell + cstride[a] : cell - cstride[a];
+    cell_spatial_dofs(G, nb, sn);
+    double hF2 = 0.0;
+    for (int b = 0; b < G.d; ++b)
+      if (b != a) hF2 += G.h[b] * G.h[b];
+    const double signK = up ? -1.0 : 1.0;
+    for (const QPoint& q : C.face[side]) {
+      double rn[3] = {q.r[0], q.r[1], q.r[2]};
+      rn[a] = up ? 0.0 : 1.0;  // the same point seen from the neighbour
+      PointBasis Bo, Bn;
+      point_basis(G, q.r, Bo);
+      point_basis(G, rn, Bn);
+      for (int mu = 0; mu < K1; ++mu) {
+        double un = 0.0;
+        for (int i = 0; i < nl; ++i) un += Uhat[st_index(G, mu, so[a * nl + i])] * Bo.phi[i];
+        const double w = P.gamma_cip * hF2 * std::fabs(un) * q.w * P.dt * C.T.w[mu];
+        for (int comp = 0; comp < G.d; ++comp) {
+          S dn_own = 0.0, dn_nb = 0.0;
+          for (int i = 0; i < nl; ++i) {
+            dn_own += X[st_index(G, mu, so[comp * nl + i])] * Bo.dphi[i][a];
+            dn_nb += X[st_index(G, mu, sn[comp * nl + i])] * Bn.dphi[i][a];
+          }
+          const S jump = up ? (dn_nb - dn_own) : (dn_own - dn_nb);
+          for (int i = 0; i < nl; ++i) Rloc[mu * ne + comp * nl + i] += scale * signK * w * jump * Bo.dphi[i][a];
+        }
+      }
+    }
+  }
+}
+
 std::vector<long> cell_list(const Geo& G, long ncells, const long* cells) {
   std::vector<long> v;
   if (cells) {
@@ -974,7 +1034,10 @@ int or_residual(const OrParams* P, const double* U, const double* vprev, const d
   const int K1 = C.G.k + 1, ne = C.G.ne;
   std::vector<double> loc((size_t)cl.size() * K1 * ne);
 #pragma omp parallel for schedule(dynamic, 16)
-  for (long c = 0; c < (long)cl.size(); ++c) cell_residual<double>(C, cl[c], U, vprev, f, gnod, &loc[c * K1 * ne]);
+  for (long c = 0; c < (long)cl.size(); ++c) {
+    cell_residual<double>(C, cl[c], U, vprev, f, gnod, &loc[c * K1 * ne]);
+    if (P->gamma_cip > 0.0) cell_cip<double>(C, cl[c], U, U, -1.0, &loc[c * K1 * ne]);  // part of the left side
+  }
   long sd[128];
   for (size_t c = 0; c < cl.size(); ++c) {
     cell_spatial_dofs(C.G, cl[c], sd);
@@ -985,7 +1048,7 @@ int or_residual(const OrParams* P, const double* U, const double* vprev, const d
 }
 
 // Complex-step residual: Rim = Im R(U + i h dU) / h (the inflow factor is
-// frozen at Re(u.n)).  Accumulates into Rim.
+// frozen at Re(u.n), the CIP weight at Re(u)).  Accumulates into Rim.
 int or_residual_cs(const OrParams* P, const double* U, const double* dU, double h, const double* vprev,
                    const double* f, const double* gnod, long ncells, const long* cells, double* Rim) {
   typedef std::complex<double> Z;
@@ -997,8 +1060,10 @@ int or_residual_cs(const OrParams* P, const double* U, const double* dU, double 
   for (long i = 0; i < C.G.Nst; ++i) Uz[i] = Z(U[i], h * dU[i]);
   std::vector<Z> loc((size_t)cl.size() * K1 * ne);
 #pragma omp parallel for schedule(dynamic, 16)
-  for (long c = 0; c < (long)cl.size(); ++c)
+  for (long c = 0; c < (long)cl.size(); ++c) {
     cell_residual<Z>(C, cl[c], Uz.data(), vprev, f, gnod, &loc[c * K1 * ne]);
+    if (P->gamma_cip > 0.0) cell_cip<Z>(C, cl[c], Uz.data(), U, -1.0, &loc[c * K1 * ne]);
+  }
   long sd[128];
   for (size_t c = 0; c < cl.size(); ++c) {
     cell_spatial_dofs(C.G, cl[c], sd);
@@ -1048,7 +1113,8 @@ int or_element_mass(const OrParams* P, int pressure, double* out) {
 }
 
 // Jacobian action out += J_n(U) dU over the given cells (cells == NULL: all),
-// by forming each cell's space-time element matrix and multiplying.
+// by forming each cell's space-time element matrix and multiplying, plus the
+// CIP term with its weight lagged at U (Sec. 4.2-4.4) when gamma_cip > 0.
 int or_jacobian_apply(const OrParams* P, int var, const double* U, const double* dU, long ncells, const long* cells,
                       double* out) {
   Ctx C;
@@ -1074,6 +1140,7 @@ int or_jacobian_apply(const OrParams* P, int var, const double* U, const double*
         for (long j = 0; j < N; ++j) s += Jst[i * N + j] * xe[j];
         loc[c * N + i] = s;
       }
+      if (P->gamma_cip > 0.0) cell_cip<double>(C, cl[c], dU, U, 1.0, &loc[c * N]);
     }
   }
   long sd[128];
@@ -1081,6 +1148,69 @@ int or_jacobian_apply(const OrParams* P, int var, const double* U, const double*
     cell_spatial_dofs(C.G, cl[c], sd);
     for (int mu = 0; mu < K1; ++mu)
       for (int i = 0; i < ne; ++i) out[st_index(C.G, mu, sd[i])] += loc[c * N + mu * ne + i];
+  }
+  return 0;
+}
+
+// CIP matrix of the slab (lagged weight at U) as dense blocks, one per
+// (cell, side, mu, comp) in that order: rows = the cell's own Q2 nodes of
+// component comp at node mu (nl slab indices), cols = own then neighbour
+// nodes (2 nl), vals[nl][2 nl].  Sides on the boundary give zero blocks (the
+// neighbour columns then repeat the own ones).  The same evaluation as
+// cell_cip with the jump expanded in the nodal values.
+int or_cip_blocks(const OrParams* P, const double* U, long* rows, long* cols, double* vals) {
+  Ctx C;
+  make_ctx(P, C);
+  const Geo& G = C.G;
+  const int K1 = G.k + 1, nl = G.nv / G.d, d = G.d;
+  const long cstride[3] = {1, (long)G.n[0], (long)G.n[0] * G.n[1]};
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long cell = 0; cell < G.ncells; ++cell) {
+    CellPos cp = cell_pos(G, cell);
+    long so[128], sn[128];
+    cell_spatial_dofs(G, cell, so);
+    for (int side = 0; side < 2 * d; ++side) {
+      const bool interior = !on_side(G, cp, side);
+      const int a = side / 2, up = side % 2;
+      const long nb = !interior ? cell : (up ? cell + cstride[a] : cell - cstride[a]);
+      cell_spatial_dofs(G, nb, sn);
+      double hF2 = 0.0;
+      for (int b = 0; b < d; ++b)
+        if (b != a) hF2 += G.h[b] * G.h[b];
+      const double signK = up ? -1.0 : 1.0;
+      for (int mu = 0; mu < K1; ++mu)
+        for (int comp = 0; comp < d; ++comp) {
+          const long blk = ((cell * 2 * d + side) * K1 + mu) * d + comp;
+          long* r = rows + blk * nl;
+          long* cc = cols + blk * 2 * nl;
+          double* v = vals + blk * 2 * nl * nl;
+          for (int i = 0; i < nl; ++i) {
+            r[i] = st_index(G, mu, so[comp * nl + i]);
+            cc[i] = r[i];
+            cc[nl + i] = st_index(G, mu, sn[comp * nl + i]);
+          }
+          for (int i = 0; i < 2 * nl * nl; ++i) v[i] = 0.0;
+          if (!interior) continue;
+          for (const QPoint& q : C.face[side]) {
+            double rn[3] = {q.r[0], q.r[1], q.r[2]};
+            rn[a] = up ? 0.0 : 1.0;
+            PointBasis Bo, Bn;
+            point_basis(G, q.r, Bo);
+            point_basis(G, rn, Bn);
+            double un = 0.0;
+            for (int i = 0; i < nl; ++i) un += U[st_index(G, mu, so[a * nl + i])] * Bo.phi[i];
+            const double w = P->gamma_cip * hF2 * std::fabs(un) * q.w * P->dt * C.T.w[mu];
+            // [d_n u] = sum_j jo[j] u_own[j] + jn[j] u_nb[j]
+            for (int i = 0; i < nl; ++i)
+              for (int j = 0; j < nl; ++j) {
+                const double jo = up ? -Bo.dphi[j][a] : Bo.dphi[j][a];
+                const double jn = up ? Bn.dphi[j][a] : -Bn.dphi[j][a];
+                v[i * 2 * nl + j] += signK * w * Bo.dphi[i][a] * jo;
+                v[i * 2 * nl + nl + j] += signK * w * Bo.dphi[i][a] * jn;
+              }
+          }
+        }
+    }
   }
   return 0;
 }

@@ -26,7 +26,7 @@ def base_params(**kw):
     p = dict(dim=3, nx=4, ny=4, nz=4, Lx=1.0, Ly=1.0, Lz=1.0, k=1, t0=0.0, dt=0.01,
              p=1.5, delta=1e-2, nu=1e-3, nu_inf=1e-4, sigma_max=1e-3,
              gamma1=1e3, gamma2=1e3, dirichlet_mask=NEUMANN_XMAX_3D, inflow_profile=0,
-             vbar=1.0, q_sign=-1.0,
+             vbar=1.0, q_sign=-1.0, gamma_cip=0.0,
              # solver parameters (library only)
              levels=1, pre_smooth=2, post_smooth=2, omega=0.25, rho_refresh=0.5,
              fgmres_restart=50, fgmres_maxit=200, newton_maxit=30, tol_abs=1e-12, tol_rel=1e-8,
