@@ -10,8 +10,9 @@
  *   - DG(k) in time, Lagrange basis on the right (k+1)-point Gauss-Radau
  *     nodes of the slab I_n = (t0, t0+dt], Sec. 3.1, Rem. 3.2;
  *   - Nitsche boundary terms B_gamma of eq. def-b-gam on Gamma_D, the
- *     convective boundary term of eq. Defc on all of Gamma; CIP is not part
- *     of this library.
+ *     convective boundary term of eq. Defc on all of Gamma;
+ *   - optional convection-aligned CIP on the interior faces, eq. scip-def
+ *     (gamma_cip > 0), h_F = the face diameter (diagonal).
  *
  * Vector layout (all vector arguments): a slab vector is
  *     U = [V_1 ... V_{k+1} | P_1 ... P_{k+1}]            (eq. slab-system)
@@ -87,6 +88,8 @@ typedef struct {
   double ew_gamma, ew_alpha, ew_max; /* Eisenstat-Walker forcing, eq. nk-inexact-newton */
   double armijo_c, lambda_min;/* Armijo backtracking on phi = 1/2 |R|_M^2 (Sec. 6.2) */
   int coarse_sweeps;          /* Vanka sweeps (exact patches) on the coarsest level  */
+  double gamma_cip;           /* CIP weight gamma_CIP of eq. scip-def; 0 = no CIP,
+                                 must be finite and >= 0                             */
 } st_params;
 
 typedef struct {
@@ -118,7 +121,8 @@ size_t st_num_dofs(const st_problem* h, int level);
 /* R = R_n(U) = -[(K_t (x) M_x) V - (m_t (x) M_x) v_prev ; 0] + (M_t (x) I) F(U)
  * (eq. slab-underint), residual convention "right-hand side minus left-hand
  * side" (eq. disc-residual).  F_mu at node t_n^mu is the spatial residual of
- * eq. disc with the form A_gamma of eq. def-a-gam (without CIP) and data
+ * eq. disc with the form A_gamma of eq. def-a-gam (plus s_CIP(u; u, .) of eq.
+ * scip-def when gamma_cip > 0) and data
  * B_gamma(g_D) of eq. def-b-gam.  v_prev: left trace u^-(t_{n-1}) (velocity
  * field); f: body force as Q2 nodal coefficients per time node ((k+1) velocity
  * fields, layout of V) or NULL.  Finest level.  prec selects the dtype of all
@@ -135,7 +139,8 @@ st_status st_linearize(st_problem* h, st_tangent tangent, const void* U);
 /* out = J_n(U) dU, eq. slab-underint-jac:
  *   J_n = [[K_t (x) M_x, 0], [0, 0]] + (M_t (x) I) diag(J_1 .. J_{k+1}),
  * J_mu the spatial linearisation with the selected tangent (Sec. 4.2-4.4,
- * eq. Jmu-block, eq. Amu-decomp without A_CIP).  U_state != NULL: linearise
+ * eq. Jmu-block, eq. Amu-decomp; A_CIP with the advecting field lagged at the
+ * linearisation state, Sec. 4.2-4.4, when gamma_cip > 0).  U_state != NULL: linearise
  * at U_state first (as st_linearize); NULL: use the last st_linearize, whose
  * tangent must equal `tangent` (else ST_EINVAL).  dU and out: slab vectors of
  * dtype prec; U_state is always double. */
@@ -152,7 +157,10 @@ st_status st_mnorm(st_problem* h, const void* r, double* out);
  * frozen at t_rep = midpoint of I_n (eq. surrogate-diag), Galerkin coarse
  * operators A_l = P^T A_{l+1} P (Sec. 6.3) and their exact cell patches,
  * inverted explicitly (batched Gauss-Jordan with partial pivoting), on every
- * level including the coarsest.  prec: FP32
+ * level including the coarsest.  With CIP the patch matrices and the
+ * Galerkin products are built from the cell-local part of the Jacobian (all
+ * but the interior-face CIP coupling), while the finest-level defects use the
+ * full Jacobian.  prec: FP32
  * (mixed) or FP64 storage/arithmetic of the smoother.  Called implicitly by
  * st_vanka_smooth / st_vcycle when missing. */
 st_status st_precond_setup(st_problem* h, st_prec prec);

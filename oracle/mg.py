@@ -21,9 +21,10 @@ restatement on the oracle's assembled matrices, small meshes only:
 Readings (the paper defers to its references here): the coarsest level is
 treated by `coarse_sweeps` additive Vanka steps with exact patches starting
 from zero; patches are cell patches; omega is a scalar.  With CIP (eq.
-scip-def) the finest-level defects use the full Jacobian, while the patch
-matrices and the Galerkin coarse operators are built from its cell-local part
-(everything but the interior-face CIP coupling).
+scip-def) the finest-level defects and the finest-level patches
+(R_K A R_K^T of the surrogate operator) include it, while the Galerkin coarse
+operators, and hence the coarse patches, are built from the cell-local part
+of the Jacobian (everything but the interior-face CIP coupling).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -114,7 +115,7 @@ def rep_state(p, U):
 
 def surrogate_operator(p, var, U):
     """Global operator whose cell patches are the surrogate patches of eq. surrogate-diag."""
-    return assemble_csr(p, var, rep_state(p, U), cip=False)
+    return assemble_csr(p, var, rep_state(p, U))
 
 
 class Hierarchy:
@@ -150,7 +151,10 @@ class Hierarchy:
         for l in range(self.levels):
             if l == L and not rebuild_finest and self.Ainv[L] is not None:
                 continue
-            src = surrogate_operator(self.p, var, U) if (l == L and self.surrogate) else self.A[l]
+            if l == L:
+                src = surrogate_operator(self.p, var, U) if self.surrogate else self.Afine
+            else:
+                src = self.A[l]
             self.Ainv[l] = [np.linalg.inv(exact_patch(src, dof)) for dof in self.dofs[l]]
 
     def op(self, l):

@@ -220,6 +220,7 @@ st_status check_params(const st_params& P, std::string& why) {
   if (!(P.p > 1.0 && P.p <= 2.0)) return why = "p must be in (1, 2]", ST_EINVAL;
   if (!(P.delta > 0 && P.nu >= 0 && P.nu_inf >= 0)) return why = "need delta > 0, nu >= 0, nu_inf >= 0", ST_EINVAL;
   if (!(P.sigma_max >= 0)) return why = "sigma_max must be >= 0", ST_EINVAL;
+  if (!(P.gamma_cip >= 0 && P.gamma_cip < 1e300)) return why = "gamma_cip must be finite and >= 0", ST_EINVAL;
   if (P.levels < 1) return why = "levels must be >= 1", ST_EINVAL;
   const long div = 1L << (P.levels - 1);
   if (P.nx % div || P.ny % div || (P.dim == 3 && P.nz % div))
@@ -279,6 +280,8 @@ void fill_op_args(const st_problem* h, int level, OpArgs& a) {
   a.inflow = P.inflow_profile;
   a.face_off = L.d_face_off;
   a.err = h->d_err;
+  a.gcip = P.gamma_cip;
+  a.cipw = nullptr;
   for (int c = 0; c < 9; ++c) a.col_start_all[c] = L.col_start[c];
   for (int c = 0; c < 8; ++c)
     for (int d = 0; d < 3; ++d) a.cn_all[c][d] = L.cn[c][d];
@@ -298,6 +301,26 @@ void prepare_op_args(const st_problem* h, int level, int prec, int tangent, cons
   a.wfcache = h->d_fcache64;
 }
 
+// CIP on the finest level of the Jacobian (lagged weights of the linearisation)
+// and of the residual (weights of its argument); off for the linearisation
+// and for the element matrices of the preconditioner
+void set_cip_args(const st_problem* h, int mode, int prec, OpArgs& a) {
+  a.cipw = nullptr;
+  if (!(h->P.gamma_cip > 0) || !h->d_cipw64) return;
+  if (mode == OP_JAC) a.cipw = prec == ST_FP64 ? (void*)h->d_cipw64 : (void*)h->d_cipw32;
+  if (mode == OP_RES) a.cipw = h->d_cipw_res;
+}
+
+cudaError_t cip_linearize(st_problem* h, const double* U, cudaStream_t st) {
+  if (!(h->P.gamma_cip > 0) || !h->d_cipw64) return cudaSuccess;
+  OpArgs a;
+  fill_op_args(h, (int)h->lev.size() - 1, a);
+  cudaError_t e = h->dim == 2 ? dispatch_cip_weights_2d(h, a, U, h->d_cipw64, st)
+                              : dispatch_cip_weights_3d(h, a, U, h->d_cipw64, st);
+  if (e == cudaSuccess) e = cast_f64_f32(h->d_cipw64, h->d_cipw32, h->cipw_len, st);
+  return e;
+}
+
 cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent, const void* in, void* out,
                       const void* vprev, const void* f) {
   OpArgs a;
@@ -311,6 +334,7 @@ cudaError_t launch_op(st_problem* h, int level, int mode, int prec, int tangent,
   a.fcache = prec == ST_FP64 ? (const void*)h->d_fcache64 : (const void*)h->d_fcache32;
   a.wcache = h->d_cache64;
   a.wfcache = h->d_fcache64;
+  if (level == (int)h->lev.size() - 1) set_cip_args(h, mode, prec, a);
   const Level& L = h->lev[level];
   return h->dim == 2 ? dispatch_op_2d(h, L, a, mode, prec, tangent) : dispatch_op_3d(h, L, a, mode, prec, tangent);
 }
@@ -403,6 +427,13 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, h->scratch_len * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_work, 3 * (size_t)F.Nst * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_Ulin, (size_t)F.Nst * sizeof(double));
+  if (h->P.gamma_cip > 0) {
+    // CIP face weights: lagged (FP64, FP32 copy) and the residual's scratch
+    h->cipw_len = (size_t)h->dim * F.ncells * h->K1 * NFQ;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cipw64, h->cipw_len * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cipw32, h->cipw_len * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cipw_res, h->cipw_len * sizeof(double));
+  }
   {
     // colour-private volume outputs; zero once: each class always writes the
     // same entries, the others stay zero
@@ -455,6 +486,9 @@ st_status st_destroy(st_problem* h) {
   cudaFree(h->d_work);
   cudaFree(h->d_Ulin);
   cudaFree(h->d_fscr);
+  cudaFree(h->d_cipw64);
+  cudaFree(h->d_cipw32);
+  cudaFree(h->d_cipw_res);
   if (h->s_face) cudaStreamDestroy(h->s_face);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -497,6 +531,8 @@ st_status st_linearize(st_problem* h, st_tangent tangent, const void* U) {
   if (s != ST_OK) return s;
   if (h->lev[L].nfaces > 0)
     s = cuda_check(h, cast_f64_f32(h->d_fcache64, h->d_fcache32, h->fcache_len, h->stream), "st_linearize cast");
+  if (s != ST_OK) return s;
+  s = cuda_check(h, cip_linearize(h, (const double*)U, h->stream), "st_linearize CIP weights");
   if (s != ST_OK) return s;
   h->lin_tangent = tangent;
   h->lin_valid = true;

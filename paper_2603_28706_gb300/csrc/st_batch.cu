@@ -148,6 +148,7 @@ st_status st_batch_linearize(st_batch* b, st_tangent tangent, const void* const*
     e = cast_f64_f32(h->d_cache64, h->d_cache32, h->cache_len, b->stream);
     if (e == cudaSuccess && h->lev.back().nfaces > 0)
       e = cast_f64_f32(h->d_fcache64, h->d_fcache32, h->fcache_len, b->stream);
+    if (e == cudaSuccess) e = cip_linearize(h, (const double*)U[i], b->stream);
     h->lin_tangent = tangent;
     h->lin_valid = true;
     h->precond_valid = false;
@@ -171,9 +172,11 @@ st_status st_batch_jacobian_apply(st_batch* b, st_tangent tangent, st_prec prec,
   }
   cudaError_t e = join_instances(b);
   std::vector<OpArgs> A(n);
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     prepare_op_args(b->inst[i], (int)b->inst[i]->lev.size() - 1, prec, tangent, dU[i], out[i], nullptr, nullptr,
                     A[i]);
+    set_cip_args(b->inst[i], OP_JAC, prec, A[i]);
+  }
   if (e == cudaSuccess) e = dispatch(b, A, OP_JAC, prec, tangent);
   if (e == cudaSuccess) e = fork_instances(b);
   return batch_cuda(b, e, "st_batch_jacobian_apply");
@@ -190,9 +193,11 @@ st_status st_batch_residual(st_batch* b, st_prec prec, const void* const* U, con
       return batch_error(b, ST_EINVAL, "st_batch_residual: a NULL vector for instance " + std::to_string(i));
   cudaError_t e = join_instances(b);
   std::vector<OpArgs> A(n);
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     prepare_op_args(b->inst[i], (int)b->inst[i]->lev.size() - 1, prec, 0, U[i], R[i], v_prev[i],
                     f ? f[i] : nullptr, A[i]);
+    set_cip_args(b->inst[i], OP_RES, prec, A[i]);
+  }
   if (e == cudaSuccess) e = dispatch(b, A, OP_RES, prec, 0);
   if (e == cudaSuccess) e = fork_instances(b);
   return batch_cuda(b, e, "st_batch_residual");

@@ -89,6 +89,10 @@ struct OpArgs {
   double* wcache;          // FP64 caches written by linearise
   double* wfcache;
   const int* face_off;     // first boundary face of every cell (linear order)
+  // CIP (eq. scip-def): gamma_CIP and the face weights (T): the lagged ones
+  // (Jacobian), or the scratch the residual fills from its argument; NULL = off
+  double gcip;
+  void* cipw;
   int* err;                // device error flag
   // colour classes (first colour-ordered index, extents); element-matrix
   // mode: fixed node mu, output matrices
@@ -167,6 +171,10 @@ struct st_problem {
   double* d_fscr = nullptr;         // compact per-face-slot outputs of the face kernel (FP64 or FP32 view)
   void* d_cbuf64 = nullptr;        // 2^dim colour-private FP64 slab vectors of the volume kernel
   void* d_cbuf32 = nullptr;        // the same in FP32 (entries no cell of a class touches stay zero)
+  double* d_cipw64 = nullptr;      // CIP face weights at the linearisation state (gamma_cip > 0 only)
+  float* d_cipw32 = nullptr;       // their FP32 copy
+  double* d_cipw_res = nullptr;    // CIP face weights of the residual's argument (FP64 or FP32 view)
+  size_t cipw_len = 0;
   cudaStream_t s_face = nullptr;   // internal stream: face kernels overlap the volume kernels
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t s_cap = nullptr;    // internal stream of the V-cycle (captured as a graph)
@@ -191,6 +199,12 @@ cudaError_t dispatch_op_batch_2d(st_problem* const* P, OpArgs* A, int n, BatchDe
 cudaError_t dispatch_op_batch_3d(st_problem* const* P, OpArgs* A, int n, BatchDev& bd, int mode, int prec,
                                  int tangent, cudaStream_t st);
 void fill_op_args(const st_problem* h, int level, OpArgs& a);
+// CIP fields of an argument block for the given mode and precision
+void set_cip_args(const st_problem* h, int mode, int prec, OpArgs& a);
+// CIP face weights of the FP64 state U into the lagged caches (FP64 and FP32)
+cudaError_t cip_linearize(st_problem* h, const double* U, cudaStream_t st);
+cudaError_t dispatch_cip_weights_2d(const st_problem* h, const OpArgs& a, const double* U, double* w, cudaStream_t st);
+cudaError_t dispatch_cip_weights_3d(const st_problem* h, const OpArgs& a, const double* U, double* w, cudaStream_t st);
 
 st_status set_error(st_problem* h, st_status s, const std::string& msg);
 st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest);

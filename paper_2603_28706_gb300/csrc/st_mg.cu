@@ -302,6 +302,109 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
   }
 }
 
+// CIP restricted to the finest-level surrogate patches (eq. scip-def at the
+// representative state): C_K = R_K S R_K^T with
+//   S = sum_F sum_q w_{F,q} c_{F,q} c_{F,q}^T,
+//   c_{F,q}[i] = d_n phi_i|upper cell(x_q) - d_n phi_i|lower cell(x_q),
+// w the face weights at Radau node 0 (they carry tau w_0, as the surrogate
+// element matrices do).  The faces whose cells share a node with K are the
+// ones normal to axis a on the planes k_a - 1 .. k_a + 2 with tangential cell
+// indices within one of K's.  C_K is the same for every velocity component;
+// it is added to S_mu with the factor w_mu / w_0, or to S_0 of every
+// time-diagonalised block.  One CTA per patch: the jump coefficients of the
+// face's quadrature points at K's nodes go to shared memory, each thread
+// accumulates up to three entries of C_K.
+struct CipPatchArgs {
+  int n[3];
+  int K1, nb, c13;
+  double ih[3];
+  double ED[6], B[9];
+  double wr[4];
+};
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) cip_patch_add(CipPatchArgs ca, const double* __restrict__ w,
+                                                     T* __restrict__ F) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NE = NC * NQ + (DIM == 3 ? 8 : 4), NFQ = DIM == 3 ? 9 : 3;
+  constexpr int R = (NQ * NQ + 255) / 256;
+  const int K1 = ca.K1, N = K1 * NE;
+  const long ncell = (long)ca.n[0] * ca.n[1] * (DIM == 3 ? ca.n[2] : 1);
+  __shared__ double sc[NFQ][NQ];
+  __shared__ double sw[NFQ];
+  for (long K = blockIdx.x; K < ncell; K += gridDim.x) {
+    const int k3[3] = {(int)(K % ca.n[0]), (int)((K / ca.n[0]) % ca.n[1]),
+                       DIM == 3 ? (int)(K / ((long)ca.n[0] * ca.n[1])) : 0};
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+      for (int P = k3[ax] - 1; P <= k3[ax] + 2; ++P) {
+        if (P < 1 || P > ca.n[ax] - 1) continue;  // boundary planes carry no CIP
+        for (int d2 = (DIM == 3 ? -1 : 0); d2 <= (DIM == 3 ? 1 : 0); ++d2)
+          for (int d1 = -1; d1 <= 1; ++d1) {
+            int u3[3] = {0, 0, 0};
+            u3[ax] = P;
+            u3[t1] = k3[t1] + d1;
+            if (DIM == 3) u3[t2] = k3[t2] + d2;
+            if (u3[t1] < 0 || u3[t1] >= ca.n[t1]) continue;
+            if (DIM == 3 && (u3[t2] < 0 || u3[t2] >= ca.n[t2])) continue;
+            __syncthreads();  // the previous face's coefficients are consumed
+            for (int it = threadIdx.x; it < NFQ * NQ; it += blockDim.x) {
+              const int q = it / NQ, i = it % NQ;
+              const int g1 = q % 3, g2 = DIM == 3 ? q / 3 : 0;
+              const int li[3] = {i % 3, (i / 3) % 3, i / 9};
+              int lu[3], ll[3];
+              bool in_u = true, in_l = true;
+              for (int d = 0; d < 3; ++d) {
+                const int G = 2 * k3[d] + li[d];
+                lu[d] = d < DIM ? G - 2 * u3[d] : 0;
+                ll[d] = d < DIM ? G - 2 * (u3[d] - (d == ax ? 1 : 0)) : 0;
+                in_u = in_u && lu[d] >= 0 && lu[d] <= 2;
+                in_l = in_l && ll[d] >= 0 && ll[d] <= 2;
+              }
+              double c = 0.0;
+              if (in_u) c += ca.ED[lu[ax]] * ca.B[g1 * 3 + lu[t1]] * (DIM == 3 ? ca.B[g2 * 3 + lu[t2]] : 1.0);
+              if (in_l) c -= ca.ED[3 + ll[ax]] * ca.B[g1 * 3 + ll[t1]] * (DIM == 3 ? ca.B[g2 * 3 + ll[t2]] : 1.0);
+              sc[q][i] = c * ca.ih[ax];
+            }
+            if (threadIdx.x < NFQ) {
+              const long up = u3[0] + (long)ca.n[0] * (u3[1] + (long)ca.n[1] * u3[2]);
+              sw[threadIdx.x] = w[(((long)ax * ncell + up) * K1) * NFQ + threadIdx.x];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int e = threadIdx.x + 256 * r;
+              if (e < NQ * NQ) {
+                const int a = e / NQ, b = e % NQ;
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < NFQ; ++q) s += sw[q] * sc[q][a] * sc[q][b];
+                acc[r] += s;
+              }
+            }
+          }
+      }
+    }
+    T* Fk = F + K * (ca.c13 ? (long)ca.nb * NE * NE * 2 : (long)N * N);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      if (e >= NQ * NQ) continue;
+      const int a = e / NQ, b = e % NQ;
+      for (int c = 0; c < NC; ++c) {
+        const int pr = c * NQ + a, pc = c * NQ + b;
+        if (ca.c13) {
+          for (int blk = 0; blk < ca.nb; ++blk) Fk[((long)(blk * NE + pc) * NE + pr) * 2] += (T)acc[r];
+        } else {
+          for (int mu = 0; mu < K1; ++mu) Fk[(long)(mu * NE + pc) * N + (mu * NE + pr)] += (T)(ca.wr[mu] * acc[r]);
+        }
+      }
+    }
+  }
+}
+
 // Colour classes of a level for one launch over all its cells in colour
 // order: class c holds the cells (c_x + 2 i, c_y + 2 j, c_z + 2 l); cells of
 // one class share no dof, so each class writes its own buffer (cb + c*stride)
@@ -1460,10 +1563,36 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
     const int estride = sur ? 1 : K1;
     const unsigned g = (unsigned)(Lv.ncells < 8L * h->nsm ? Lv.ncells : 8L * h->nsm);
     const long nblk = Lv.ncells * (long)m->te.nb;
+    // CIP in the surrogate patches: face weights at the representative state
+    const bool cip = sur && h->P.gamma_cip > 0 && h->d_cipw_res;
+    CipPatchArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    if (cip) {
+      for (int d = 0; d < 3; ++d) {
+        ca.n[d] = Lv.n[d];
+        ca.ih[d] = 1.0 / Lv.h[d];
+      }
+      ca.K1 = K1;
+      ca.nb = pa.nb;
+      ca.c13 = pa.c13;
+      for (int i = 0; i < 6; ++i) ca.ED[i] = h->R.ED[i];
+      for (int i = 0; i < 9; ++i) ca.B[i] = h->R.B[i];
+      for (int mu = 0; mu < K1; ++mu) ca.wr[mu] = pa.wr[mu];
+      OpArgs wa;
+      fill_op_args(h, l, wa);
+      e = h->dim == 2 ? dispatch_cip_weights_2d(h, wa, m->Urep, h->d_cipw_res, h->stream)
+                      : dispatch_cip_weights_3d(h, wa, m->Urep, h->d_cipw_res, h->stream);
+      if (e != cudaSuccess) break;
+    }
     if (prec == ST_FP64) {
       if (h->dim == 2) patch_assemble<2, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
       else patch_assemble<3, double><<<g, 256, 0, h->stream>>>((const double*)Esrc, estride, pa, (double*)m->L[l].LU);
       e = cudaGetLastError();
+      if (e == cudaSuccess && cip) {
+        if (h->dim == 2) cip_patch_add<2, double><<<g, 256, 0, h->stream>>>(ca, h->d_cipw_res, (double*)m->L[l].LU);
+        else cip_patch_add<3, double><<<g, 256, 0, h->stream>>>(ca, h->d_cipw_res, (double*)m->L[l].LU);
+        e = cudaGetLastError();
+      }
       if (e == cudaSuccess)
         e = c13 ? invert_patches_cplx<double>((double*)m->L[l].LU, NE, nblk, h->d_err, h->nsm, h->stream)
                 : invert_patches<double>((double*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);
@@ -1471,6 +1600,11 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
       if (h->dim == 2) patch_assemble<2, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       else patch_assemble<3, float><<<g, 256, 0, h->stream>>>((const float*)Esrc, estride, pa, (float*)m->L[l].LU);
       e = cudaGetLastError();
+      if (e == cudaSuccess && cip) {
+        if (h->dim == 2) cip_patch_add<2, float><<<g, 256, 0, h->stream>>>(ca, h->d_cipw_res, (float*)m->L[l].LU);
+        else cip_patch_add<3, float><<<g, 256, 0, h->stream>>>(ca, h->d_cipw_res, (float*)m->L[l].LU);
+        e = cudaGetLastError();
+      }
       if (e == cudaSuccess)
         e = c13 ? invert_patches_cplx<float>((float*)m->L[l].LU, NE, nblk, h->d_err, h->nsm, h->stream)
                 : invert_patches<float>((float*)m->L[l].LU, m->L[l].piv, N, Lv.ncells, h->d_err, h->nsm, h->stream);

@@ -13,6 +13,9 @@ cudaError_t dispatch_op_batch_2d(st_problem* const* P, OpArgs* A, int n, BatchDe
                                  int tangent, cudaStream_t st) {
   return dispatch_op_batch_dim<2>(P, A, n, bd, mode, prec, tangent, st);
 }
+cudaError_t dispatch_cip_weights_2d(const st_problem* h, const OpArgs& a, const double* U, double* w, cudaStream_t st) {
+  return dispatch_cip_weights_dim<2>(h, a, U, w, st);
+}
 cudaError_t upload_consts_2d(const ConstTables& t, const ConstTablesF& tf) {
   cudaError_t e = cudaMemcpyToSymbol(cT, &t, sizeof(t));
   if (e != cudaSuccess) return e;

@@ -3,6 +3,7 @@
 
 #include <vector>
 
+#include "st_cip.cuh"
 #include "st_face.cuh"
 #include "st_operator.cuh"
 
@@ -56,6 +57,43 @@ cudaError_t launch_node_sum_t(const st_problem* h, const Level& L, const OpArgs&
   return cudaGetLastError();
 }
 
+// CIP face terms added into the class buffers (after the volume kernel, before
+// the node sum); the residual first fills its weights from its argument
+template <int DIM, int K1, typename T, int MODE>
+cudaError_t launch_cip_t(const st_problem* h, const Level& L, const OpArgs& a, cudaStream_t st) {
+  if (MODE != OP_JAC && MODE != OP_RES) return cudaSuccess;
+  if (!a.cipw || L.ncells == 0) return cudaSuccess;
+  T* w = reinterpret_cast<T*>(a.cipw);
+  if (MODE == OP_RES) {
+    long g = ((long)DIM * L.ncells * K1 + 255) / 256;
+    if (g > 16L * h->nsm) g = 16L * h->nsm;
+    st_cip_weights<DIM, K1, T><<<(unsigned)g, 256, 0, st>>>(a, reinterpret_cast<const T*>(a.in), w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  long g = ((long)DIM * L.ncells * K1 + 127) / 128;
+  if (g > 16L * h->nsm) g = 16L * h->nsm;
+  st_cip_apply<DIM, K1, T><<<(unsigned)g, 128, 0, st>>>(a, w, MODE == OP_RES ? (T)-1 : (T)1);
+  return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t dispatch_cip_weights_dim(const st_problem* h, const OpArgs& a, const double* U, double* w,
+                                     cudaStream_t st) {
+  const Level& L = h->lev.back();
+  long g = ((long)DIM * L.ncells * h->K1 + 255) / 256;
+  if (g > 16L * h->nsm) g = 16L * h->nsm;
+  if (g < 1) return cudaSuccess;
+  switch (h->K1) {
+    case 1: st_cip_weights<DIM, 1, double><<<(unsigned)g, 256, 0, st>>>(a, U, w); break;
+    case 2: st_cip_weights<DIM, 2, double><<<(unsigned)g, 256, 0, st>>>(a, U, w); break;
+    case 3: st_cip_weights<DIM, 3, double><<<(unsigned)g, 256, 0, st>>>(a, U, w); break;
+    case 4: st_cip_weights<DIM, 4, double><<<(unsigned)g, 256, 0, st>>>(a, U, w); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // the volume kernel's view of the whole finest level
 template <typename T>
 void set_volume_args(const st_problem* h, const Level& L, OpArgs& a) {
@@ -95,6 +133,8 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  e = launch_cip_t<DIM, K1, T, MODE>(h, L, a, h->stream);
+  if (e != cudaSuccess) return e;
   e = cudaEventRecord(h->ev_join, h->s_face);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   if (e != cudaSuccess) return e;
@@ -130,8 +170,10 @@ cudaError_t launch_op_batch_t(st_problem* const* P, OpArgs* A, int n, BatchDev& 
   const long grid = first[n] < cap ? (first[n] > 0 ? first[n] : 1) : cap;
   kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, st>>>(bd.d_desc, bd.d_first, n, bd.d_queue);
   e = cudaGetLastError();
-  for (int i = 0; i < n && e == cudaSuccess && MODE != OP_LIN; ++i)
-    e = launch_node_sum_t<DIM, K1, T>(P[i], P[i]->lev.back(), A[i], st);
+  for (int i = 0; i < n && e == cudaSuccess && MODE != OP_LIN; ++i) {
+    e = launch_cip_t<DIM, K1, T, MODE>(P[i], P[i]->lev.back(), A[i], st);
+    if (e == cudaSuccess) e = launch_node_sum_t<DIM, K1, T>(P[i], P[i]->lev.back(), A[i], st);
+  }
   return e;
 }
 
