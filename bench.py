@@ -225,6 +225,59 @@ def batched_comparison(st, torch):
     return res
 
 
+CIP_GAMMA = 1.0
+
+
+def cip_comparison(st, torch, p, Ud, dUd, stream, apply_ms_plain=None):
+    """The FP64 modN Jacobian apply of the bench workload with the CIP term
+    (eq. scip-def, gamma_CIP = 1, weights lagged at the state) against the
+    same apply without it; the difference is the cost of st_cip_apply."""
+    q = dict(p, gamma_cip=CIP_GAMMA)
+    prob = st.Problem(q, stream=stream)
+    out = torch.empty_like(dUd)
+    reps = 50
+
+    def timed(pr):
+        pr.linearize(st.ST_MODN, Ud)
+        for _ in range(3):
+            pr.jacobian_apply(st.ST_MODN, dUd, out=out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pr.jacobian_apply(st.ST_MODN, dUd, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_cip = timed(prob)
+    if apply_ms_plain is None:
+        plain = st.Problem(p, stream=stream)
+        apply_ms_plain = timed(plain)
+        plain.close()
+    prob.close()
+    s = oracle_sizes(p)
+    K1, d = p["k"] + 1, p["dim"]
+    ncells = s["ncells"]
+    nfq = 9 if d == 3 else 3
+    # read the velocity of dU, read the face weights, write the velocity result
+    alg = 8 * (2 * K1 * s["Mv"] + d * ncells * K1 * nfq)
+    dt = t_cip - apply_ms_plain
+    return {"gamma_cip": CIP_GAMMA, "apply_ms": t_cip, "apply_ms_plain": apply_ms_plain, "cip_ms": dt,
+            "cip_algorithmic_bytes": alg, "cip_gbs": alg / (dt * 1e-3) / 1e9 if dt > 0 else None,
+            "kernels": "st_cip_apply<3,2,double> (one thread per cell, component and Radau node; adds into the "
+                       "colour-class buffers before the node sum)"}
+
+
+def oracle_sizes(p):
+    """Slab sizes of a parameter dict (plain arithmetic, no oracle call)."""
+    d = p["dim"]
+    n = [p["nx"], p["ny"]] + ([p["nz"]] if d == 3 else [])
+    nq2 = int(np.prod([2 * m + 1 for m in n]))
+    return {"Mv": d * nq2, "ncells": int(np.prod(n))}
+
+
 class ClockSampler:
     def __init__(self, index):
         self.index = index
@@ -333,6 +386,8 @@ def main():
     ap.add_argument("--newton-only", action="store_true", help="run only the Newton-step comparison and print it")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instance comparison")
     ap.add_argument("--batched-only", action="store_true", help="run only the batched-instance comparison")
+    ap.add_argument("--no-cip", action="store_true", help="skip the apply with the CIP term")
+    ap.add_argument("--cip-only", action="store_true", help="run only the apply with and without the CIP term")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     args = ap.parse_args()
@@ -356,6 +411,10 @@ def main():
         print(json.dumps(batched_comparison(st, torch)))
         return
     stream = torch.cuda.current_stream()
+    if args.cip_only:
+        print(json.dumps(cip_comparison(st, torch, p, torch.from_numpy(U).cuda(), torch.from_numpy(dU).cuda(),
+                                        stream)))
+        return
     prob = st.Problem(p, stream=stream)
     n = prob.num_dofs()
     Ud = torch.from_numpy(U).cuda()
@@ -442,6 +501,7 @@ def main():
     e2e = {"value": ws * n * len(tangents) * APPLIES / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": len(tangents) * 2 * 8 * n, "d2h_bytes_per_step": len(tangents) * 8 * n}
 
+    cip = None if (args.no_cip or rank != 0) else cip_comparison(st, torch, p, Ud, dUd, stream, apply_ms)
     newton = None if (args.no_newton or rank != 0) else newton_comparison(st, torch, tuple(args.newton_mesh))
     batched = None if (args.no_batched or rank != 0) else batched_comparison(st, torch)
 
@@ -466,7 +526,7 @@ def main():
                                  (8 * 2 * 32768 * 27 * 11 / 1e6),
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
-                "newton": newton, "batched": batched,
+                "cip": cip, "newton": newton, "batched": batched,
                 "clocks": clk.summary()}
         print(json.dumps(line))
     prob.close()
