@@ -225,6 +225,92 @@ def batched_comparison(st, torch):
     return res
 
 
+SWEEP_WORKLOAD = ("2D channel 4x1, 4n x n cells (n in SWEEP_MESHES), Q2/Q1, dG(1), dt=1, parabolic Nitsche inflow "
+                  "vbar=0.1 at x=0, no-slip walls, do-nothing outflow, nu=1e-3, nu_inf=0, sigma_max=1e-4; initial "
+                  "velocity: the "
+                  "parabolic inflow profile plus 0.1 x an 8-mode Fourier field (seed 7); SWEEP_SLABS slabs, each "
+                  "slab's Newton step started from the previous solution, |R|_M <= 1e-8 |R0|_M, at most 30 "
+                  "iterations, FP32 V-cycle (levels down to 2 cells across)")
+SWEEP_P = (1.5, 1.33, 1.25, 1.2, 1.16)
+SWEEP_DELTA = (1e-5, 1e-10)
+SWEEP_MESHES = (4, 8, 16, 32)
+SWEEP_SLABS = 4
+SWEEP_VARIANTS = ("Pic", "exN", "modN")
+
+
+def work(fgmres_iters, ndofs):
+    """Work of eq. work: the FGMRES iterations of all nonlinear iterations of
+    all time slabs times the space-time dofs per slab."""
+    return float(sum(fgmres_iters)) * ndofs
+
+
+def perf_profile(W, taus):
+    """Dolan-More profile of eq. perf-profile.  W[i][s]: work of variant s on
+    instance i (inf = not solved).  Returns pi[s][j] = fraction of instances
+    with W[i][s] <= taus[j] * min_s' W[i][s'] (an instance no variant solves
+    counts as unsolved for all)."""
+    W = np.asarray(W, dtype=float)
+    best = W.min(axis=1)
+    ok = np.isfinite(best)
+    r = np.full(W.shape, np.inf)
+    r[ok] = W[ok] / best[ok, None]
+    return [[float(np.mean(r[:, s] <= t)) for t in taus] for s in range(W.shape[1])]
+
+
+def sweep_instance(st, torch, p, tangent, slabs, vprec):
+    """Time-march `slabs` slabs with one Newton step each; returns the Newton
+    counts per slab, the FGMRES iterations and the work, or the failure."""
+    prob = st.Problem(p)
+    n, nv, K1 = prob.num_dofs(), prob.velocity_size(), p["k"] + 1
+    vprev = torch.from_numpy(si.developed_channel_velocity(p, 7).reshape(-1)).cuda()
+    U = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for mu in range(K1):
+        U[mu * nv:(mu + 1) * nv] = vprev
+    n_nl, n_l, status, fail = [], [], st.ST_OK, None
+    for _ in range(slabs):
+        status, info = prob.newton_step(tangent, U, vprev, vcycle_prec=vprec, raise_on_fail=False)
+        if status != st.ST_OK:
+            fail = {"slab": len(n_nl), "newton_iters": info["newton_iters"], "fgmres_iters": info["fgmres_iters_total"],
+                    "res_ratio": info["res_norm_final"] / max(info["res_norm_initial"], 1e-300)}
+            break
+        n_nl.append(info["newton_iters"])
+        n_l.append(info["fgmres_iters_total"])
+        vprev = U[(K1 - 1) * nv: K1 * nv].clone()  # u^-(t_n): the right Radau node is t_n
+    prob.close()
+    ok = status == st.ST_OK
+    return {"ok": ok, "status": int(status), "n_nl": n_nl, "n_l": n_l, "ndofs": n, "failure": fail,
+            "W": work(n_l, n) if ok else None, "n_nl_mean": float(np.mean(n_nl)) if ok else None}
+
+
+def robustness_sweep(st, torch, vprec_name="fp32"):
+    """Analogue of the solver evaluation of Sec. 7 (Table newton-compact, eq.
+    work, eq. perf-profile) on synthetic channel problems: every (p, delta,
+    mesh) instance with Pic, exN and modN."""
+    tangents = {"Pic": st.ST_PIC, "exN": st.ST_EXN, "modN": st.ST_MODN}
+    vprec = st.ST_FP32 if vprec_name == "fp32" else st.ST_FP64
+    inst, W = [], []
+    t0 = time.perf_counter()
+    for n in SWEEP_MESHES:
+        levels = int(np.log2(n))
+        for delta in SWEEP_DELTA:
+            for pe in SWEEP_P:
+                prm = si.base_params(dim=2, nx=4 * n, ny=n, Lx=4.0, Ly=1.0, k=1, dt=1.0, p=pe, delta=delta,
+                                     nu=1e-3, nu_inf=0.0, sigma_max=1e-4, inflow_profile=1, vbar=0.1,
+                                     levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30)
+                row = {"cells": 4 * n * n, "p": pe, "delta": delta}
+                for v in SWEEP_VARIANTS:
+                    row[v] = sweep_instance(st, torch, prm, tangents[v], SWEEP_SLABS, vprec)
+                inst.append(row)
+                W.append([row[v]["W"] if row[v]["ok"] else np.inf for v in SWEEP_VARIANTS])
+    taus = [1.0, 1.25, 1.5, 2.0, 3.0, 5.0, 10.0]
+    prof = perf_profile(W, taus)
+    return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "meshes_cells": [4 * n * n for n in SWEEP_MESHES],
+            "p": list(SWEEP_P),
+            "delta": list(SWEEP_DELTA), "slabs": SWEEP_SLABS, "wall_s": time.perf_counter() - t0,
+            "instances": inst, "taus": taus, "profile": dict(zip(SWEEP_VARIANTS, prof)),
+            "solved": {v: float(np.mean([np.isfinite(w[j]) for w in W])) for j, v in enumerate(SWEEP_VARIANTS)}}
+
+
 CIP_GAMMA = 1.0
 
 
@@ -388,6 +474,9 @@ def main():
     ap.add_argument("--batched-only", action="store_true", help="run only the batched-instance comparison")
     ap.add_argument("--no-cip", action="store_true", help="skip the apply with the CIP term")
     ap.add_argument("--cip-only", action="store_true", help="run only the apply with and without the CIP term")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run only the robustness sweep (Pic / exN / modN over (p, delta, mesh)) and print it")
+    ap.add_argument("--sweep-vcycle", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the sweep")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     args = ap.parse_args()
@@ -409,6 +498,9 @@ def main():
         return
     if args.batched_only:
         print(json.dumps(batched_comparison(st, torch)))
+        return
+    if args.sweep:
+        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle)))
         return
     stream = torch.cuda.current_stream()
     if args.cip_only:

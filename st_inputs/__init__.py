@@ -113,6 +113,23 @@ def fourier_velocity(p, seed, nmodes=8, kmax=4):
     return out
 
 
+def developed_channel_velocity(p, seed, eps=0.1):
+    """A developed channel flow with a perturbation, velocity field (d, Nq2):
+    the parabolic inflow profile vbar 6 y(1-y) [6 z(1-z)] (scaled coordinates,
+    constant in x) plus eps vbar times the Fourier field of node 0, so that
+    the shear rate is nonzero almost everywhere."""
+    X = q2_node_coords(p)
+    d = p["dim"]
+    y = X[:, 1] / p["Ly"]
+    prof = p["vbar"] * 6.0 * y * (1.0 - y)
+    if d == 3:
+        z = X[:, 2] / p["Lz"]
+        prof = prof * 6.0 * z * (1.0 - z)
+    v = eps * p["vbar"] * fourier_velocity(p, seed)[0]
+    v[0] += prof
+    return v
+
+
 def fourier_state(p, seed):
     """Smooth random velocity (8 Fourier modes) + uniform pressure, as one slab vector."""
     s = sizes(p)
