@@ -317,7 +317,8 @@ CIP_GAMMA = 1.0
 def cip_comparison(st, torch, p, Ud, dUd, stream, apply_ms_plain=None):
     """The FP64 modN Jacobian apply of the bench workload with the CIP term
     (eq. scip-def, gamma_CIP = 1, weights lagged at the state) against the
-    same apply without it; the difference is the cost of st_cip_apply."""
+    same apply without it; the difference is the cost of st_cip_face and
+    st_cip_apply."""
     q = dict(p, gamma_cip=CIP_GAMMA)
     prob = st.Problem(q, stream=stream)
     out = torch.empty_like(dUd)
@@ -352,7 +353,8 @@ def cip_comparison(st, torch, p, Ud, dUd, stream, apply_ms_plain=None):
     dt = t_cip - apply_ms_plain
     return {"gamma_cip": CIP_GAMMA, "apply_ms": t_cip, "apply_ms_plain": apply_ms_plain, "cip_ms": dt,
             "cip_algorithmic_bytes": alg, "cip_gbs": alg / (dt * 1e-3) / 1e9 if dt > 0 else None,
-            "kernels": "st_cip_apply<3,2,double> (one thread per cell, component and Radau node; adds into the "
+            "kernels": "st_cip_face<3,2,double> (every interior face once: weighted, tested jumps into a face "
+                       "buffer) + st_cip_apply<3,2,double> (per cell: the one-sided expansions, added into the "
                        "colour-class buffers before the node sum)"}
 
 

@@ -433,6 +433,8 @@ st_status st_setup_mesh(const st_params* params, void* cuda_stream, st_problem**
     if (e == cudaSuccess) e = cudaMalloc(&h->d_cipw64, h->cipw_len * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_cipw32, h->cipw_len * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_cipw_res, h->cipw_len * sizeof(double));
+    // tested face jumps: per face, component and node the 3^(dim-1) face-plane values
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_cipf, h->cipw_len * h->dim * sizeof(double));
   }
   {
     // colour-private volume outputs; zero once: each class always writes the
@@ -489,6 +491,7 @@ st_status st_destroy(st_problem* h) {
   cudaFree(h->d_cipw64);
   cudaFree(h->d_cipw32);
   cudaFree(h->d_cipw_res);
+  cudaFree(h->d_cipf);
   if (h->s_face) cudaStreamDestroy(h->s_face);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);

@@ -4,7 +4,7 @@
 // normal to axis a, [w] = w on the upper cell minus w on the lower one, h_F the
 // face diameter (diagonal), 3-point Gauss quadrature per tangential direction.
 //
-// Two kernels:
+// Three kernels:
 //   st_cip_weights  gamma_CIP h_F^2 |uhat_a| x face-quadrature weight x tau w_mu
 //                   at the Gauss points of every interior face, from the velocity
 //                   of a slab vector (the linearisation state for the lagged
@@ -12,12 +12,16 @@
 //                   Layout w[((a * ncells + upper cell) * K1 + mu) * NFQ + g],
 //                   g = g1 + 3 g2 along the face's tangential axes in increasing
 //                   order; entries of cells on the lower boundary stay zero.
-//   st_cip_apply    one thread per (cell, component, Radau node): the cell's
-//                   own share of the face terms of its 2*DIM faces.  The jump of
-//                   a test function is the difference of its one-sided traces,
-//                   so the cell adds sign_K * w * [d_n u] * d_n phi_i|K to its own
+//   st_cip_face     every interior face once: the jump of d_n u at the face
+//                   Gauss points, weighted and tested against the face-plane
+//                   nodes (9 values per face, component and node, into a face
+//                   buffer); one thread per (cell, component, node) does the
+//                   faces below its cell.
+//   st_cip_apply    one thread per (cell, component, node): the jump of a test
+//                   function is the difference of its one-sided traces, so the
+//                   cell adds sign_K d_n phi_i|K times the face values to its own
 //                   nodes (sign_K = +1 on its lower face, where it is the upper
-//                   cell, -1 on its upper face).  The result is added into the
+//                   cell, -1 on its upper face), and adds the result into the
 //                   private buffer of the cell's colour class after the volume
 //                   kernel has stored there: cells of one class share no node.
 #pragma once
@@ -98,46 +102,88 @@ __global__ void st_cip_weights(const OpArgs a, const T* __restrict__ U, T* __res
   }
 }
 
-// the cell's share of the face normal to AX on its lower (UP = 0) or upper side
-template <int DIM, int K1, typename T, int AX, int UP>
-__device__ __forceinline__ void cip_face(const OpArgs& a, const T* __restrict__ x, const T* __restrict__ w,
-                                         const T* u, T* y, long base, long cell, long nc, const int* e3, int mu) {
+// Per interior face normal to AX (index = its upper cell), component c and
+// node mu: the weighted jump tested against the face-plane nodes,
+//   f = B^T (w o B [d_n u]),   [d_n u] = d_n u|upper - d_n u|lower at the
+// face-plane nodes, B the Q2 values at the tangential Gauss points.  Both
+// cells' tests are +-(d_n phi) expansions of f, formed by st_cip_apply.
+// Layout fb[(((AX * K1 + mu) * DIM + c) * NFQ + tn) * ncells + upper cell].
+template <int DIM, int K1, typename T, int AX>
+__device__ __forceinline__ void cip_face_values(const OpArgs& a, const T* __restrict__ x, const T* __restrict__ w,
+                                                T* __restrict__ fb, long cell, long nc, const int* e3, int c, int mu) {
   constexpr int NFQ = Dims<DIM>::NFQ;
-  if constexpr (AX >= DIM) return;
-  if (UP == 0 ? e3[AX] == 0 : e3[AX] == a.n[AX] - 1) return;  // boundary face
   const auto& ct = CT<T>::t();
   const long s[3] = {1, a.g2[0], a.g2[0] * a.g2[1]};
-  const long cs[3] = {1, a.n[0], (long)a.n[0] * a.n[1]};
-  const T* xn = x + (UP ? base + 2 * s[AX] : base - 2 * s[AX]);
+  const long base = 2L * e3[0] + a.g2[0] * (2L * e3[1] + a.g2[1] * 2L * e3[2]);
+  const T* xu = x + base;                // upper cell (this one)
+  const T* xl = x + base - 2 * s[AX];    // lower cell
   const T ih = (T)a.ih[AX];
   T j[NFQ];
 #pragma unroll
   for (int tn = 0; tn < NFQ; ++tn) {
     const int p1 = tn % 3, p2 = DIM == 3 ? tn / 3 : 0;
-    T dno = 0, dnn = 0;
+    T du = 0, dl = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int q = cip_lnode<AX>(i, p1, p2);
-      dno += (T)ct.ED[UP * 3 + i] * u[q];
-      dnn += (T)ct.ED[(1 - UP) * 3 + i] * xn[cip_goff(a, q)];
+      du += (T)ct.ED[i] * xu[cip_goff(a, q)];
+      dl += (T)ct.ED[3 + i] * xl[cip_goff(a, q)];
     }
-    j[tn] = (UP ? dnn - dno : dno - dnn) * ih;  // [d_n u] at the face-plane nodes
+    j[tn] = (du - dl) * ih;
   }
   cip_tpass<DIM>(j, ct.B);
-  const T* wf = w + (((long)AX * nc + (UP ? cell + cs[AX] : cell)) * K1 + mu) * NFQ;
+  const T* wf = w + (((long)AX * nc + cell) * K1 + mu) * NFQ;
 #pragma unroll
-  for (int g = 0; g < NFQ; ++g) j[g] *= UP ? -wf[g] : wf[g];
+  for (int g = 0; g < NFQ; ++g) j[g] *= wf[g];
   cip_tpass<DIM>(j, ct.Bt);
+  T* o = fb + ((((long)AX * K1 + mu) * DIM + c) * NFQ) * nc + cell;
 #pragma unroll
-  for (int tn = 0; tn < NFQ; ++tn) {
-    const int p1 = tn % 3, p2 = DIM == 3 ? tn / 3 : 0;
+  for (int tn = 0; tn < NFQ; ++tn) o[(long)tn * nc] = j[tn];
+}
+
+// one thread per (cell, component, node): the faces below the cell in every
+// direction (the cell is their upper cell)
+template <int DIM, int K1, typename T>
+__global__ void __launch_bounds__(128) st_cip_face(const OpArgs a, const T* __restrict__ w, T* __restrict__ fb) {
+  const long nc = (long)a.n[0] * a.n[1] * (DIM == 3 ? a.n[2] : 1);
+  const long total = nc * DIM * K1;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long cell = t % nc;
+    const int r = (int)(t / nc), c = r % DIM, mu = r / DIM;
+    const int e3[3] = {(int)(cell % a.n[0]), (int)((cell / a.n[0]) % a.n[1]),
+                       DIM == 3 ? (int)(cell / ((long)a.n[0] * a.n[1])) : 0};
+    const T* x = reinterpret_cast<const T*>(a.in) + (long)mu * a.Mv + (long)c * a.Nq2;
+    if (e3[0] > 0) cip_face_values<DIM, K1, T, 0>(a, x, w, fb, cell, nc, e3, c, mu);
+    if (e3[1] > 0) cip_face_values<DIM, K1, T, 1>(a, x, w, fb, cell, nc, e3, c, mu);
+    if constexpr (DIM == 3)
+      if (e3[2] > 0) cip_face_values<DIM, K1, T, 2>(a, x, w, fb, cell, nc, e3, c, mu);
+  }
+}
+
+// the cell's test of the face normal to AX on its lower (UP = 0: the cell is
+// the upper cell, sign +) or upper side (sign -): y += sign d_n phi_i f
+template <int DIM, int K1, typename T, int AX, int UP>
+__device__ __forceinline__ void cip_expand(const OpArgs& a, const T* __restrict__ fb, T* y, long cell, long nc,
+                                           const int* e3, int c, int mu) {
+  constexpr int NFQ = Dims<DIM>::NFQ;
+  if constexpr (AX < DIM) {
+    if (UP == 0 ? e3[AX] == 0 : e3[AX] == a.n[AX] - 1) return;  // boundary face
+    const auto& ct = CT<T>::t();
+    const long cs[3] = {1, a.n[0], (long)a.n[0] * a.n[1]};
+    const T* f = fb + ((((long)AX * K1 + mu) * DIM + c) * NFQ) * nc + (UP ? cell + cs[AX] : cell);
+    const T ih = (T)a.ih[AX];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) y[cip_lnode<AX>(i, p1, p2)] += (T)ct.ED[UP * 3 + i] * ih * j[tn];
+    for (int tn = 0; tn < NFQ; ++tn) {
+      const int p1 = tn % 3, p2 = DIM == 3 ? tn / 3 : 0;
+      const T v = UP ? -f[(long)tn * nc] : f[(long)tn * nc];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) y[cip_lnode<AX>(i, p1, p2)] += (T)ct.ED[UP * 3 + i] * ih * v;
+    }
   }
 }
 
 template <int DIM, int K1, typename T>
-__global__ void __launch_bounds__(128) st_cip_apply(const OpArgs a, const T* __restrict__ w, T sgn) {
+__global__ void __launch_bounds__(128) st_cip_apply(const OpArgs a, const T* __restrict__ fb, T sgn) {
   constexpr int NQ = Dims<DIM>::NQ;
   const long nc = (long)a.n[0] * a.n[1] * (DIM == 3 ? a.n[2] : 1);
   const long total = nc * DIM * K1;
@@ -147,19 +193,15 @@ __global__ void __launch_bounds__(128) st_cip_apply(const OpArgs a, const T* __r
     const int e3[3] = {(int)(cell % a.n[0]), (int)((cell / a.n[0]) % a.n[1]),
                        DIM == 3 ? (int)(cell / ((long)a.n[0] * a.n[1])) : 0};
     const long base = 2L * e3[0] + a.g2[0] * (2L * e3[1] + a.g2[1] * 2L * e3[2]);
-    const T* x = reinterpret_cast<const T*>(a.in) + (long)mu * a.Mv + (long)c * a.Nq2;
-    T u[NQ], y[NQ];
+    T y[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      u[q] = x[base + cip_goff(a, q)];
-      y[q] = (T)0;
-    }
-    cip_face<DIM, K1, T, 0, 0>(a, x, w, u, y, base, cell, nc, e3, mu);
-    cip_face<DIM, K1, T, 0, 1>(a, x, w, u, y, base, cell, nc, e3, mu);
-    cip_face<DIM, K1, T, 1, 0>(a, x, w, u, y, base, cell, nc, e3, mu);
-    cip_face<DIM, K1, T, 1, 1>(a, x, w, u, y, base, cell, nc, e3, mu);
-    cip_face<DIM, K1, T, 2, 0>(a, x, w, u, y, base, cell, nc, e3, mu);
-    cip_face<DIM, K1, T, 2, 1>(a, x, w, u, y, base, cell, nc, e3, mu);
+    for (int q = 0; q < NQ; ++q) y[q] = (T)0;
+    cip_expand<DIM, K1, T, 0, 0>(a, fb, y, cell, nc, e3, c, mu);
+    cip_expand<DIM, K1, T, 0, 1>(a, fb, y, cell, nc, e3, c, mu);
+    cip_expand<DIM, K1, T, 1, 0>(a, fb, y, cell, nc, e3, c, mu);
+    cip_expand<DIM, K1, T, 1, 1>(a, fb, y, cell, nc, e3, c, mu);
+    cip_expand<DIM, K1, T, 2, 0>(a, fb, y, cell, nc, e3, c, mu);
+    cip_expand<DIM, K1, T, 2, 1>(a, fb, y, cell, nc, e3, c, mu);
     T* ob = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(e3[0], e3[1], e3[2]) * a.cbuf_stride +
             (long)mu * a.Mv + (long)c * a.Nq2 + base;
 #pragma unroll

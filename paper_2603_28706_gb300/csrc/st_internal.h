@@ -174,6 +174,7 @@ struct st_problem {
   double* d_cipw64 = nullptr;      // CIP face weights at the linearisation state (gamma_cip > 0 only)
   float* d_cipw32 = nullptr;       // their FP32 copy
   double* d_cipw_res = nullptr;    // CIP face weights of the residual's argument (FP64 or FP32 view)
+  double* d_cipf = nullptr;        // CIP tested face jumps of one apply (FP64 or FP32 view)
   size_t cipw_len = 0;
   cudaStream_t s_face = nullptr;   // internal stream: face kernels overlap the volume kernels
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

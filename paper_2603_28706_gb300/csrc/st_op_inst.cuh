@@ -73,7 +73,11 @@ cudaError_t launch_cip_t(const st_problem* h, const Level& L, const OpArgs& a, c
   }
   long g = ((long)DIM * L.ncells * K1 + 127) / 128;
   if (g > 16L * h->nsm) g = 16L * h->nsm;
-  st_cip_apply<DIM, K1, T><<<(unsigned)g, 128, 0, st>>>(a, w, MODE == OP_RES ? (T)-1 : (T)1);
+  T* fb = reinterpret_cast<T*>(h->d_cipf);
+  st_cip_face<DIM, K1, T><<<(unsigned)g, 128, 0, st>>>(a, w, fb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  st_cip_apply<DIM, K1, T><<<(unsigned)g, 128, 0, st>>>(a, fb, MODE == OP_RES ? (T)-1 : (T)1);
   return cudaGetLastError();
 }
 
