@@ -262,9 +262,31 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
       T S[4] = {0, 0, 0, 0};
       double mass = 0.0;
       const bool vel_pair = p < NC * NQ && q < NC * NQ && (p / NQ) == (q / NQ);
-      for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
+      // neighbour shifts that hold both dofs, per axis (bit delta + 1): a Q2
+      // node index 0 / 1 / 2 lies in the shifts {-1, 0} / {0} / {0, 1}, a Q1
+      // node index 0 / 1 in {-1, 0} / {0, 1}; the cells that do not are skipped
+      // without their index arithmetic, in the same order as before
+      int am[3] = {2, 2, 2};
+      {
+        int ip[3], iq[3];
+        const bool vp = p < NC * NQ, vq = q < NC * NQ;
+        const int np_ = vp ? p % NQ : p - NC * NQ, nq_ = vq ? q % NQ : q - NC * NQ;
+        for (int d = 0; d < 3; ++d) {
+          ip[d] = vp ? (d == 0 ? np_ % 3 : d == 1 ? (np_ / 3) % 3 : np_ / 9) : ((np_ >> d) & 1);
+          iq[d] = vq ? (d == 0 ? nq_ % 3 : d == 1 ? (nq_ / 3) % 3 : nq_ / 9) : ((nq_ >> d) & 1);
+        }
+        for (int d = 0; d < DIM; ++d) {
+          const int mp = vp ? (ip[d] == 0 ? 3 : ip[d] == 1 ? 2 : 6) : (ip[d] == 0 ? 3 : 6);
+          const int mq = vq ? (iq[d] == 0 ? 3 : iq[d] == 1 ? 2 : 6) : (iq[d] == 0 ? 3 : 6);
+          am[d] = mp & mq;
+        }
+      }
+      for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+        if (!((am[2] >> (dz + 1)) & 1)) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+          if (!((am[1] >> (dy + 1)) & 1)) continue;
           for (int dx = -1; dx <= 1; ++dx) {
+            if (!((am[0] >> (dx + 1)) & 1)) continue;
             const int dl[3] = {dx, dy, dz};
             const int e3[3] = {k3[0] + dx, k3[1] + dy, k3[2] + dz};
             bool inside = true;
@@ -281,6 +303,8 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
             }
             if (vel_pair) mass += smass[(lp % NQ) * NQ + (lq % NQ)];
           }
+        }
+      }
       if (pa.c13) {
         // block b: lambda_b M_v + S_0 (S_0: the surrogate block of node 0), complex, column-major
         for (int b = 0; b < pa.nb; ++b) {
