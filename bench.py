@@ -413,6 +413,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+def replica_throughput(ms_local, dofs, applies, device="cpu"):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (MAX over ranks when torch.distributed is initialised with more than one
+    rank) and every rank's dofs x applies over it."""
+    import torch
+    ws = 1
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+    ms = float(ms_local)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * dofs * applies / (ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -538,13 +554,8 @@ def main():
             step()
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     applies = args.steps * len(tangents) * APPLIES
-    value = ws * n * applies / (ms * 1e-3)
+    ms, value = replica_throughput(e0.elapsed_time(e1), n, applies, device="cuda")
 
     # dominant kernel: the FP64 Jacobian apply, timed alone with events on its stream
     prob.linearize(st.ST_MODN, Ud)
