@@ -138,3 +138,20 @@ def test_cip_off_is_the_plain_operator():
     np.testing.assert_array_equal(oracle.jacobian_apply(p, oracle.MODN, U, X),
                                   oracle.jacobian_apply(dict(p, gamma_cip=0.0), oracle.MODN, U, X))
     assert oracle.cip_csr(dict(p, gamma_cip=0.0), U).count_nonzero() == 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_jacobian_is_the_derivative_with_the_weight_frozen(dim):
+    # with the CIP weight (and the inflow factor) frozen at Re(u), the complex
+    # step of the residual is the exN Jacobian with the lagged CIP term
+    p = si.base_params(k=1, gamma_cip=1.3, **mesh(dim))
+    s = oracle.sizes(p)
+    U = si.uniform_state(p, 3)
+    dU = si.uniform_state(p, 4)
+    vp = si.uniform(s["Mv"], 5)
+    J = oracle.jacobian_apply(p, oracle.EXN, U, dU)
+    cs = -oracle.residual_cs(p, U, dU, 1e-30, vprev=vp)
+    assert np.abs(J - cs).max() <= 1e-13 * np.abs(J).max()
+    # and the CIP part is not negligible in it
+    J0 = oracle.jacobian_apply(dict(p, gamma_cip=0.0), oracle.EXN, U, dU)
+    assert np.abs(J - J0).max() > 1e-3 * np.abs(J).max()
