@@ -11,7 +11,8 @@ the Jacobian (Sec. 4.2-4.4).
     S x = 0;
   * the lagged matrix is symmetric positive semidefinite (the property the
     paper states below eq. Amu-decomp);
-  * the assembled face blocks and the matrix-free cell evaluation agree.
+  * the assembled face blocks and the matrix-free cell evaluation agree;
+  * with the weight frozen, the complex step of the residual is the Jacobian.
 """
 import numpy as np
 import pytest
