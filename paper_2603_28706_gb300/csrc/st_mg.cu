@@ -1096,19 +1096,26 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
       skt[mu][v] = acc;
     }
     __syncthreads();
-    // one warp per row: coalesced row of E, then the temporal mass coupling
-    for (int r = warp; r < N; r += nwarp) {
-      const int mu = r / NE, i = r % NE;
+    // one half-warp per row (two rows per warp): coalesced row of E, then the
+    // temporal mass coupling; the loop runs over whole warps so that every
+    // lane takes part in the half-warp shuffles
+    const int hl = lane & 15, half = lane >> 4;
+    for (int r0 = 2 * warp; r0 < N; r0 += 2 * nwarp) {
+      const int r = r0 + half;
+      const bool act = r < N;
+      const int mu = act ? r / NE : 0, i = act ? r % NE : 0;
       const T* Er = E + (cell * K1 + mu) * NE * NE + (long)i * NE;
       T acc = 0;
-      for (int j = lane; j < NE; j += 32) acc = fma(Er[j], sx[mu * NE + j], acc);
-      if (i < NC * NQ) {
-        const int c = i / NQ, a = i % NQ;
-        for (int bq = lane; bq < NQ; bq += 32) acc = fma(smass[a * NQ + bq], skt[mu][c * NQ + bq], acc);
+      if (act) {
+        for (int j = hl; j < NE; j += 16) acc = fma(Er[j], sx[mu * NE + j], acc);
+        if (i < NC * NQ) {
+          const int c = i / NQ, a = i % NQ;
+          for (int bq = hl; bq < NQ; bq += 16) acc = fma(smass[a * NQ + bq], skt[mu][c * NQ + bq], acc);
+        }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) ob[sg[r]] = acc;
+      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (act && hl == 0) ob[sg[r]] = acc;
     }
     __syncthreads();
   }
