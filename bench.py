@@ -282,7 +282,7 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
             "W": work(n_l, n) if ok else None, "n_nl_mean": float(np.mean(n_nl)) if ok else None}
 
 
-def robustness_sweep(st, torch, vprec_name="fp32"):
+def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate"):
     """Analogue of the solver evaluation of Sec. 7 (Table newton-compact, eq.
     work, eq. perf-profile) on synthetic channel problems: every (p, delta,
     mesh) instance with Pic, exN and modN."""
@@ -296,7 +296,8 @@ def robustness_sweep(st, torch, vprec_name="fp32"):
             for pe in SWEEP_P:
                 prm = si.base_params(dim=2, nx=4 * n, ny=n, Lx=4.0, Ly=1.0, k=1, dt=1.0, p=pe, delta=delta,
                                      nu=1e-3, nu_inf=0.0, sigma_max=1e-4, inflow_profile=1, vbar=0.1,
-                                     levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30)
+                                     levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30,
+                                     finest_patches=0 if patches == "surrogate" else 1)
                 row = {"cells": 4 * n * n, "p": pe, "delta": delta}
                 for v in SWEEP_VARIANTS:
                     row[v] = sweep_instance(st, torch, prm, tangents[v], SWEEP_SLABS, vprec)
@@ -304,7 +305,8 @@ def robustness_sweep(st, torch, vprec_name="fp32"):
                 W.append([row[v]["W"] if row[v]["ok"] else np.inf for v in SWEEP_VARIANTS])
     taus = [1.0, 1.25, 1.5, 2.0, 3.0, 5.0, 10.0]
     prof = perf_profile(W, taus)
-    return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "meshes_cells": [4 * n * n for n in SWEEP_MESHES],
+    return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "finest_patches": patches,
+            "meshes_cells": [4 * n * n for n in SWEEP_MESHES],
             "p": list(SWEEP_P),
             "delta": list(SWEEP_DELTA), "slabs": SWEEP_SLABS, "wall_s": time.perf_counter() - t0,
             "instances": inst, "taus": taus, "profile": dict(zip(SWEEP_VARIANTS, prof)),
@@ -495,6 +497,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="run only the robustness sweep (Pic / exN / modN over (p, delta, mesh)) and print it")
     ap.add_argument("--sweep-vcycle", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the sweep")
+    ap.add_argument("--sweep-patches", default="surrogate", choices=["surrogate", "exact"],
+                    help="finest-level Vanka patches of the sweep: the surrogate of eq. surrogate-diag or exact")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     args = ap.parse_args()
@@ -518,7 +522,7 @@ def main():
         print(json.dumps(batched_comparison(st, torch)))
         return
     if args.sweep:
-        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle)))
+        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches)))
         return
     stream = torch.cuda.current_stream()
     if args.cip_only:

@@ -90,6 +90,10 @@ typedef struct {
   int coarse_sweeps;          /* Vanka sweeps (exact patches) on the coarsest level  */
   double gamma_cip;           /* CIP weight gamma_CIP of eq. scip-def; 0 = no CIP,
                                  must be finite and >= 0                             */
+  int finest_patches;         /* 0: surrogate patches on the finest level (eq.
+                                 surrogate-diag, Sec. 6.3); 1: exact patches
+                                 R_K J_n R_K^T of the linearisation, under the same
+                                 refresh rule (not with gamma_cip > 0)               */
 } st_params;
 
 typedef struct {
@@ -157,7 +161,8 @@ st_status st_mnorm(st_problem* h, const void* r, double* out);
  * frozen at t_rep = midpoint of I_n (eq. surrogate-diag), Galerkin coarse
  * operators A_l = P^T A_{l+1} P (Sec. 6.3) and their exact cell patches,
  * inverted explicitly (batched Gauss-Jordan with partial pivoting), on every
- * level including the coarsest.  With CIP the patch matrices and the
+ * level including the coarsest (finest_patches = 1: exact finest patches
+ * instead of the surrogate ones).  With CIP the patch matrices and the
  * Galerkin products are built from the cell-local part of the Jacobian (all
  * but the interior-face CIP coupling), while the finest-level defects use the
  * full Jacobian.  prec: FP32

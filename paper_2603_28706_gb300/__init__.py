@@ -39,7 +39,7 @@ class StParams(ctypes.Structure):
                 ("tol_abs", ctypes.c_double), ("tol_rel", ctypes.c_double), ("lin_rtol", ctypes.c_double),
                 ("ew_gamma", ctypes.c_double), ("ew_alpha", ctypes.c_double), ("ew_max", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("lambda_min", ctypes.c_double),
-                ("coarse_sweeps", ctypes.c_int), ("gamma_cip", ctypes.c_double)]
+                ("coarse_sweeps", ctypes.c_int), ("gamma_cip", ctypes.c_double), ("finest_patches", ctypes.c_int)]
 
 
 class StNewtonInfo(ctypes.Structure):
@@ -112,8 +112,11 @@ def load(build_if_missing=True):
     return lib
 
 
+_OPTIONAL = {"gamma_cip": 0.0, "finest_patches": 0}
+
+
 def params(p):
-    return StParams(*[p.get(name, 0.0) if name == "gamma_cip" else p[name] for name, _ in StParams._fields_])
+    return StParams(*[p.get(name, _OPTIONAL[name]) if name in _OPTIONAL else p[name] for name, _ in StParams._fields_])
 
 
 def _ptr(t, dtype=None, n=None, name="vector"):

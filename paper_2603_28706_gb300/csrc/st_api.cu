@@ -221,6 +221,9 @@ st_status check_params(const st_params& P, std::string& why) {
   if (!(P.delta > 0 && P.nu >= 0 && P.nu_inf >= 0)) return why = "need delta > 0, nu >= 0, nu_inf >= 0", ST_EINVAL;
   if (!(P.sigma_max >= 0)) return why = "sigma_max must be >= 0", ST_EINVAL;
   if (!(P.gamma_cip >= 0 && P.gamma_cip < 1e300)) return why = "gamma_cip must be finite and >= 0", ST_EINVAL;
+  if (P.finest_patches != 0 && P.finest_patches != 1) return why = "finest_patches must be 0 or 1", ST_EINVAL;
+  if (P.finest_patches == 1 && P.gamma_cip > 0)
+    return why = "exact finest patches (finest_patches = 1) do not carry the CIP term", ST_EINVAL;
   if (P.levels < 1) return why = "levels must be >= 1", ST_EINVAL;
   const long div = 1L << (P.levels - 1);
   if (P.nx % div || P.ny % div || (P.dim == 3 && P.nz % div))

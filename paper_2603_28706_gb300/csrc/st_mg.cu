@@ -1241,7 +1241,7 @@ void free_mg(MgState* m) {
 }
 
 cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
-  m->c13 = make_time_eig(h->T, m->te) && m->te.nb <= MAX_K1;
+  m->c13 = h->P.finest_patches == 0 && make_time_eig(h->T, m->te) && m->te.nb <= MAX_K1;
   const int nl = (int)h->lev.size();
   const int NE = ne_of(h->dim), K1 = h->K1, N = K1 * NE;
   const size_t es = esz(prec);
@@ -1507,14 +1507,16 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
   const int tangent = h->lin_tangent;
   const void* cache = prec == ST_FP64 ? (const void*)h->d_cache64 : (const void*)h->d_cache32;
   const void* fcache = prec == ST_FP64 ? (const void*)h->d_fcache64 : (const void*)h->d_fcache32;
-  // finest level: exact element matrices per node (for the Galerkin operators)
-  if (nl > 1)
+  // finest level: exact element matrices per node (for the Galerkin operators
+  // and the exact finest patches)
+  const bool exact_finest = h->P.finest_patches == 1;
+  if (nl > 1 || exact_finest)
     for (int mu = 0; mu < K1 && e == cudaSuccess; ++mu)
       e = prec == ST_FP64 ? elm_dispatch<double>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc)
                           : elm_dispatch<float>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc);
   if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup element matrices");
   // representative state and its coefficients -> surrogate matrices
-  if (rebuild_finest) {
+  if (rebuild_finest && !exact_finest) {
     const double* lr = h->T.lrep;
     rep_state_kernel<<<gridn(F.Mv + F.Mp, h->nsm), 256, 0, h->stream>>>(
         h->d_Ulin, m->Urep, K1, F.Mv, (long)K1 * F.Mp, lr[0], K1 > 1 ? lr[1] : 0.0, K1 > 2 ? lr[2] : 0.0,
@@ -1578,8 +1580,8 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
   e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
   for (int l = 0; l < nl && e == cudaSuccess; ++l) {
     const Level& Lv = h->lev[l];
-    const bool sur = (l == L);
-    if (sur && !rebuild_finest) continue;  // refresh rule: keep the surrogate factorisations
+    const bool sur = (l == L) && !exact_finest;
+    if (l == L && !rebuild_finest) continue;  // refresh rule: keep the finest factorisations
     PatchArgs pa = patch_args(h, l, sur);
     const bool c13 = sur && m->c13;
     if (c13) {

@@ -125,3 +125,28 @@ def test_vcycle_graph_replay_is_bitwise_equal():
             outs.append(d.clone())
         assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2]), prec
     prob.close()
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=8, ny=4, k=1, levels=2, inflow_profile=1),
+                                  dict(dim=3, nx=4, ny=4, nz=4, k=1, levels=2)])
+def test_vcycle_exact_finest_patches(case):
+    # finest_patches = 1: the finest level's patches are R_K J R_K^T of the
+    # linearisation (the oracle hierarchy with surrogate=False), inverted as
+    # real patches instead of the time-diagonalised surrogate
+    p = si.base_params(p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, coarse_sweeps=4, finest_patches=1,
+                       **case)
+    st = gpu()
+    U = smooth_state(p)
+    r = si.uniform(oracle.sizes(p)["Nst"], 1)
+    H = mg.Hierarchy(p, VAR[2], U, p["levels"], p["omega"], p["pre_smooth"], p["post_smooth"],
+                     coarse_sweeps=p["coarse_sweeps"], surrogate=False)
+    ref = H.vcycle(r)
+    Hs = mg.Hierarchy(p, VAR[2], U, p["levels"], p["omega"], p["pre_smooth"], p["post_smooth"],
+                      coarse_sweeps=p["coarse_sweeps"], surrogate=True)
+    assert np.abs(Hs.vcycle(r) - ref).max() > 1e-6 * np.abs(ref).max()  # the two modes differ
+    prob = st.Problem(p)
+    prob.linearize(2, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        d = prob.vcycle(dev(r, dt), prec=prec)
+        assert rel(d, ref) <= tol, (prec, rel(d, ref))
+    prob.close()

@@ -103,3 +103,20 @@ def test_channel_newton_final_residual_by_oracle(prec):
     assert rf <= 1.0001e-8 * r0, (rf / r0, info)
     prob.close()
 
+
+
+def test_newton_exact_finest_patches_matches_oracle():
+    st = gpu()
+    p = dict(problem(2), finest_patches=1)
+    U0, vprev = start(p)
+    Uo, info = kr.newton(p, oracle.MODN, U0, vprev, vcycle_levels=p["levels"], max_iter=40, tol_rel=p["tol_rel"],
+                         tol_abs=p["tol_abs"], omega=p["omega"], coarse_sweeps=p["coarse_sweeps"], surrogate=False)
+    assert info["status"] == "ok"
+    prob = st.Problem(p)
+    for prec in (st.ST_FP64, st.ST_FP32):
+        U = dev(U0)
+        status, ginfo = prob.newton_step(2, U, dev(vprev), vcycle_prec=prec)
+        assert status == st.ST_OK, ginfo
+        err = np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+        assert err <= 1e-8, (prec, err, ginfo, info["iters"])
+    prob.close()
