@@ -58,7 +58,8 @@ class OrParams(ctypes.Structure):
                 ("nu_inf", ctypes.c_double), ("sigma_max", ctypes.c_double),
                 ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
                 ("dirichlet_mask", ctypes.c_uint), ("inflow_profile", ctypes.c_int),
-                ("vbar", ctypes.c_double), ("q_sign", ctypes.c_double), ("gamma_cip", ctypes.c_double)]
+                ("vbar", ctypes.c_double), ("q_sign", ctypes.c_double), ("gamma_cip", ctypes.c_double),
+                ("pressure_space", ctypes.c_int)]
 
 
 _lib = None
@@ -90,9 +91,12 @@ def lib():
     return _lib
 
 
+_OPTIONAL = {"gamma_cip": 0.0, "pressure_space": 0}
+
+
 def params(p):
     """OrParams from a parameter dict (see st_inputs.base_params)."""
-    return OrParams(*[p.get(name, 0.0) if name == "gamma_cip" else p[name] for name, _ in OrParams._fields_])
+    return OrParams(*[p.get(name, _OPTIONAL[name]) if name in _OPTIONAL else p[name] for name, _ in OrParams._fields_])
 
 
 def _d(a):

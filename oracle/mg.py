@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain numpy/scipy
 restatement on the oracle's assembled matrices, small meshes only:
 
   prolongation       nested Q2/Q1 transfer P: coarse finite-element function
-                     evaluated at the fine nodes; identity in time (same k on
-                     all levels); restriction = P^T
+                     evaluated at the fine nodes (P1disc pressure: the
+                     coarse cell's linear function in the children's bases);
+                     identity in time (same k on all levels); restriction = P^T
   galerkin           A_l = P^T A_{l+1} P (Petrov-Galerkin with Pi = P^T)
   patch_dofs         cell patch K: every velocity and pressure dof of cell K at
                      every Radau node (the full time-step block)
@@ -67,6 +68,32 @@ def prolongation_1d(nc, order):
     return P
 
 
+def prolongation_p1disc(pc):
+    """P1disc pressure prolongation (fine coefficients x coarse coefficients):
+    on a child cell with offset o in {0,1}^d of its parent, the parent's basis
+    2 r_c - 1 with r_c = (r_f + o)/2 is (2 r_f - 1)/2 + o - 1/2, so
+    c_f0 = c_c0 + sum_j c_cj (o_j - 1/2) and c_fj = c_cj / 2 (exact: the
+    spaces are nested)."""
+    d = pc["dim"]
+    n = [pc["nx"], pc["ny"]] + ([pc["nz"]] if d == 3 else [])
+    nf = [2 * m for m in n]
+    nl = d + 1
+    rows, cols, vals = [], [], []
+    for fc in range(int(np.prod(nf))):
+        fi = [fc % nf[0], (fc // nf[0]) % nf[1]] + ([fc // (nf[0] * nf[1])] if d == 3 else [])
+        ci = [f // 2 for f in fi]
+        o = [f % 2 for f in fi]
+        cc = ci[0] + n[0] * (ci[1] + (n[1] * ci[2] if d == 3 else 0))
+        rows.append(fc * nl)
+        cols.append(cc * nl)
+        vals.append(1.0)
+        for j in range(d):
+            rows += [fc * nl, fc * nl + 1 + j]
+            cols += [cc * nl + 1 + j, cc * nl + 1 + j]
+            vals += [o[j] - 0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(int(np.prod(nf)) * nl, int(np.prod(n)) * nl))
+
+
 def prolongation(pc):
     """Slab prolongation from the mesh of pc to the twice finer mesh."""
     d = pc["dim"]
@@ -82,7 +109,7 @@ def prolongation(pc):
     for m in reversed(P1[:-1]):
         Pp = np.kron(Pp, m)
     Pv = sp.csr_matrix(Pv)
-    Pp = sp.csr_matrix(Pp)
+    Pp = prolongation_p1disc(pc) if pc.get("pressure_space", 0) == 1 else sp.csr_matrix(Pp)
     blocks = [Pv] * (K1 * d) + [Pp] * K1
     return sp.block_diag(blocks, format="csr")
 

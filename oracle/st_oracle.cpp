@@ -18,7 +18,10 @@
 // Discretisation (readings of the paper, shared with the CUDA path only as
 // mathematics):
 //   * uniform box mesh [0,Lx]x[0,Ly](x[0,Lz]) of nx x ny (x nz) cells;
-//   * Q2 continuous velocity, Q1 continuous pressure (Taylor-Hood, Sec. 3.1);
+//   * Q2 continuous velocity; Q1 continuous pressure (Taylor-Hood, Sec. 3.1)
+//     or, with pressure_space = 1, the discontinuous P1 pressure of the
+//     paper's experiments (Q2/P1disc, Sec. 7): per cell the basis 1 and
+//     2 r_a - 1 (r_a the reference coordinates), cell-wise dofs;
 //   * tensor 3-point Gauss quadrature in cells, 3x3 on faces;
 //   * DG(k) in time, Lagrange basis on right Gauss-Radau nodes (Sec. 3.1,
 //     Rem. 3.2); time integrals by the (k+1)-point Radau rule (Sec. 5.2);
@@ -58,6 +61,7 @@ struct OrParams {
   double vbar;
   double q_sign;            // coefficient of (u.n, q)_{Gamma_D} in B^s
   double gamma_cip;         // CIP weight gamma_CIP of eq. scip-def (0: no CIP)
+  int pressure_space;       // 0: Q1 continuous (Taylor-Hood); 1: P1disc (Sec. 7)
 };
 }
 
@@ -204,6 +208,7 @@ struct Geo {
   long Nq2, Nq1, Mv, Mp, Nst;
   int nv, np, ne;  // local velocity dofs, local pressure dofs, total per node
   long ncells;
+  bool pdisc;      // P1disc pressure
 };
 
 Geo make_geo(const OrParams& P) {
@@ -230,6 +235,11 @@ Geo make_geo(const OrParams& P) {
     G.ncells *= nn[a];
     nloc2 *= G.l2[a];
     nloc1 *= G.l1[a];
+  }
+  G.pdisc = P.pressure_space == 1;
+  if (G.pdisc) {
+    nloc1 = G.d + 1;                      // 1, 2 r_0 - 1, .., 2 r_{d-1} - 1 on every cell
+    G.Nq1 = G.ncells * (long)nloc1;
   }
   G.Mv = G.d * G.Nq2;
   G.Mp = G.Nq1;
@@ -265,6 +275,10 @@ void cell_spatial_dofs(const Geo& G, long cell, long* out) {
           long gx = 2L * c.e[0] + x, gy = 2L * c.e[1] + y, gz = (G.d == 3) ? 2L * c.e[2] + z : 0;
           out[idx++] = comp * G.Nq2 + gx + G.g2[0] * (gy + G.g2[1] * gz);
         }
+  if (G.pdisc) {
+    for (int j = 0; j < G.np; ++j) out[idx++] = G.Mv + cell * G.np + j;
+    return;
+  }
   for (int z = 0; z < G.l1[2]; ++z)
     for (int y = 0; y < G.l1[1]; ++y)
       for (int x = 0; x < G.l1[0]; ++x) {
@@ -284,7 +298,7 @@ long st_index(const Geo& G, int mu, long sidx) {
 // its reference coordinates r[a] in the cell (absent directions: unused).
 struct PointBasis {
   double phi[27], dphi[27][3];  // Q2 scalar basis
-  double psi[8];                // Q1 basis
+  double psi[8];                // pressure basis (Q1, or P1disc)
 };
 
 const double Q2N[3] = {0.0, 0.5, 1.0};
@@ -316,6 +330,11 @@ void point_basis(const Geo& G, const double r[3], PointBasis& B) {
         ++idx;
       }
   idx = 0;
+  if (G.pdisc) {
+    B.psi[idx++] = 1.0;
+    for (int a = 0; a < G.d; ++a) B.psi[idx++] = 2.0 * r[a] - 1.0;
+    return;
+  }
   for (int z = 0; z < G.l1[2]; ++z)
     for (int y = 0; y < G.l1[1]; ++y)
       for (int x = 0; x < G.l1[0]; ++x) B.psi[idx++] = v1[0][x] * v1[1][y] * v1[2][z];

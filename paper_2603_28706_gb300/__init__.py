@@ -116,6 +116,8 @@ _OPTIONAL = {"gamma_cip": 0.0, "finest_patches": 0}
 
 
 def params(p):
+    if p.get("pressure_space", 0) != 0:
+        raise ValueError("the CUDA library implements the Q2/Q1 pair only (pressure_space = 0)")
     return StParams(*[p.get(name, _OPTIONAL[name]) if name in _OPTIONAL else p[name] for name, _ in StParams._fields_])
 
 
