@@ -19,6 +19,7 @@ Functions and the passages they follow:
                      from its face blocks; residual and jacobian_apply include
                      it when p["gamma_cip"] > 0
   mnorm2             block mass-weighted norm of Sec. 6.1
+  div_norm2          squared L2(L2) norm of div u over the slab (Table conv-pns)
   pointwise          S(A), DS(A)(B), the three tangents (Sec. 2, 4.2-4.4)
   time_tables        right Gauss-Radau nodes/weights, K_t, m_t, M_t (Sec. 5.2)
 """
@@ -88,6 +89,8 @@ def lib():
         _lib.or_time_tables.argtypes = [ctypes.c_int, d, d, d, d, d]
         _lib.or_gauss01.argtypes = [ctypes.c_int, d, d]
         _lib.or_cip_blocks.argtypes = [P, d, L, L, d]
+        _lib.or_div_norm2.argtypes = [P, d]
+        _lib.or_div_norm2.restype = ctypes.c_double
     return _lib
 
 
@@ -214,6 +217,11 @@ def element_mass(p, pressure=False):
     out = np.zeros((n, n))
     lib().or_element_mass(ctypes.byref(params(p)), int(pressure), _d(out))
     return out
+
+
+def div_norm2(p, U):
+    """Squared L2(I_n; L2) norm of div u over the slab (Radau rule in time)."""
+    return lib().or_div_norm2(ctypes.byref(params(p)), _d(_f64(U)))
 
 
 def mnorm2(p, r):

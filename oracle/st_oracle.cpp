@@ -1234,6 +1234,32 @@ int or_cip_blocks(const OrParams* P, const double* U, long* rows, long* cols, do
   return 0;
 }
 
+// Squared L2(I_n; L2(Omega)) norm of div u over the slab, by the cell Gauss
+// rule in space and the Radau rule in time: sum_mu tau w_mu (div u_mu, div u_mu)
+// (the divergence error of Table conv-pns; the exact velocity is solenoidal).
+double or_div_norm2(const OrParams* P, const double* U) {
+  Ctx C;
+  make_ctx(P, C);
+  const Geo& G = C.G;
+  const int K1 = G.k + 1, nl = G.nv / G.d;
+  double total = 0.0;
+  long sd[128];
+  for (long cell = 0; cell < G.ncells; ++cell) {
+    cell_spatial_dofs(G, cell, sd);
+    for (const QPoint& q : C.vol) {
+      PointBasis B;
+      point_basis(G, q.r, B);
+      for (int mu = 0; mu < K1; ++mu) {
+        double dv = 0.0;
+        for (int comp = 0; comp < G.d; ++comp)
+          for (int i = 0; i < nl; ++i) dv += U[st_index(G, mu, sd[comp * nl + i])] * B.dphi[i][comp];
+        total += P->dt * C.T.w[mu] * q.w * dv * dv;
+      }
+    }
+  }
+  return total;
+}
+
 // Block mass-weighted squared norm (Sec. 6.1), literal reading:
 //   r_v^T (M_t (x) M_x) r_v + r_p^T (M_t (x) M_{x,p}) r_p,  M_t = tau diag(w)
 double or_mnorm2(const OrParams* P, const double* r) {

@@ -8,7 +8,9 @@ reference coordinates), cell-wise dofs.
     P1disc, written in the cell basis by hand);
   * the multigrid prolongation maps a global linear pressure's coarse
     coefficients to its fine ones, and P^T M_f P = M_c for the pressure mass;
-  * the manufactured solution of Sec. 7.1 converges with P1disc as with Q1.
+  * the manufactured solution of Sec. 7.1 converges with P1disc as with Q1,
+    and its divergence error (Table conv-pns) decays at about second order;
+  * the slab divergence norm itself against a closed form.
 """
 import numpy as np
 import pytest
@@ -117,6 +119,16 @@ def test_manufactured_solution_converges_with_p1disc():
 def _slab_error(p, uf, ff, t0=0.5, tau=0.01):
     s = oracle.sizes(p)
     X = si.q2_node_coords(p)
+    ones = np.ones(len(X))
+    U = _slab_solution(p, uf, ff, t0, tau)
+    uex = np.concatenate([uf[c](X[:, 0], X[:, 1], t0 + tau) * ones for c in range(2)])
+    return np.abs(U[s["Mv"]: 2 * s["Mv"]] - uex).max()
+
+
+def _slab_solution(p, uf, ff, t0=0.5, tau=0.01):
+    """Newton solve of the first slab of the manufactured problem (pressure constant removed)."""
+    s = oracle.sizes(p)
+    X = si.q2_node_coords(p)
     T = oracle.time_tables(1)
     ones = np.ones(len(X))
     f = np.concatenate([np.concatenate([ff[c](X[:, 0], X[:, 1], t0 + tau * tm) * ones for c in range(2)])
@@ -134,5 +146,32 @@ def _slab_error(p, uf, ff, t0=0.5, tau=0.01):
         U[keep] += dU
         if np.abs(dU).max() < 1e-12:
             break
-    uex = np.concatenate([uf[c](X[:, 0], X[:, 1], t0 + tau) * ones for c in range(2)])
-    return np.abs(U[s["Mv"]: 2 * s["Mv"]] - uex).max()
+    return U
+
+
+def test_div_norm_closed_form():
+    # u = (x^2, y) has div u = 2x + 1: int over [0,Lx]x[0,Ly] of (2x+1)^2 = Ly ((2Lx+1)^3 - 1) / 6,
+    # and the Radau weights sum to one, so the slab norm is tau times that
+    p = si.base_params(dim=2, nx=3, ny=2, Lx=1.5, Ly=0.5, k=2, dt=0.3)
+    X = si.q2_node_coords(p)
+    s = oracle.sizes(p)
+    v = np.concatenate([X[:, 0] ** 2, X[:, 1]])
+    U = np.concatenate([np.tile(v, 3), np.zeros(3 * s["Mp"])])
+    expect = p["dt"] * p["Ly"] * ((2 * p["Lx"] + 1) ** 3 - 1) / 6
+    assert oracle.div_norm2(p, U) == pytest.approx(expect, rel=1e-13)
+
+
+def test_divergence_error_decays_quadratically():
+    # the divergence error of Table conv-pns under uniform refinement, for the
+    # P1disc pair of the paper and for Q2/Q1: both close to second order
+    sy = pytest.importorskip("sympy")  # noqa: F841
+    import test_oracle_manufactured as tm
+    pp, dl, nu, nui = 1.5, 0.1, 0.1, 0.0
+    uf, ff = tm.manufactured(pp, dl, nu, nui)
+    for ps in (1, 0):
+        e = []
+        for n in (4, 8, 16):
+            p = si.base_params(dim=2, nx=n, ny=n, k=1, t0=0.5, dt=0.01, p=pp, delta=dl, nu=nu, nu_inf=nui,
+                               sigma_max=np.inf, dirichlet_mask=si.ALL_SIDES_2D, pressure_space=ps)
+            e.append(np.sqrt(oracle.div_norm2(p, _slab_solution(p, uf, ff))))
+        assert e[0] / e[1] > 3.0 and e[1] / e[2] > 3.5, (ps, e)
