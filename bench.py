@@ -12,6 +12,13 @@ value = space-time DoFs x applies / second, inputs resident in HBM.
 cells per step).  Under torchrun (N > 1) every rank runs an independent
 replica (the single-slab apply has no data-parallel split); value sums the
 ranks' DoFs over the max-over-ranks time.
+
+Besides the timed step, the line carries (rank 0): the roofline of the apply,
+the end-to-end rate with host buffers, the oracle's CPU rate, the apply with
+the CIP term (`cip`), the mixed vs FP64 Newton step on the 128x32x32 channel
+(`newton`) and the batched instances (`batched`).  Separate modes print one
+object each: --cip-only, --newton-only, --batched-only, and --sweep (the
+Pic / exN / modN robustness sweep with work and Dolan-More profiles).
 """
 import argparse
 import json
