@@ -162,18 +162,20 @@ st_status st_mnorm(st_problem* h, const void* r, double* out);
  * operators A_l = P^T A_{l+1} P (Sec. 6.3) and their exact cell patches,
  * inverted explicitly (batched Gauss-Jordan with partial pivoting), on every
  * level including the coarsest (finest_patches = 1: exact finest patches
- * instead of the surrogate ones).  With CIP the patch matrices and the
- * Galerkin products are built from the cell-local part of the Jacobian (all
- * but the interior-face CIP coupling), while the finest-level defects use the
- * full Jacobian.  prec: FP32
- * (mixed) or FP64 storage/arithmetic of the smoother.  Called implicitly by
+ * instead of the surrogate ones).  With CIP the finest-level defects and
+ * the finest surrogate patches include it (R_K S R_K^T of the CIP matrix at
+ * the representative state), while the Galerkin coarse operators and their
+ * patches are built from the cell-local part of the Jacobian (all but the
+ * interior-face CIP coupling).  prec: FP32 (mixed) or FP64
+ * storage/arithmetic of the smoother.  Called implicitly by
  * st_vanka_smooth / st_vcycle when missing. */
 st_status st_precond_setup(st_problem* h, st_prec prec);
 
 /* `sweeps` additive Vanka steps on level `level` (eq. stmg-vanka-update):
  *   d <- d + omega sum_K R_K^T A_K^{-1} R_K (r - A_l d),
  * cell patches K with all k+1 time nodes; A_K exact on coarse levels and the
- * surrogate of eq. surrogate-diag on the finest level.  r, d: slab vectors of
+ * surrogate of eq. surrogate-diag on the finest level (exact there too with
+ * finest_patches = 1).  r, d: slab vectors of
  * that level, dtype prec; d is updated in place. */
 st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, const void* r, void* d);
 
