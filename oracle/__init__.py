@@ -22,6 +22,9 @@ Functions and the passages they follow:
   div_norm2          squared L2(L2) norm of div u over the slab (Table conv-pns)
   pointwise          S(A), DS(A)(B), the three tangents (Sec. 2, 4.2-4.4)
   time_tables        right Gauss-Radau nodes/weights, K_t, m_t, M_t (Sec. 5.2)
+
+Parameters beyond the CUDA library's: pressure_space = 1 selects the Q2/P1disc
+pair of the paper's experiments (Sec. 7) instead of Q2/Q1.
 """
 import ctypes
 import os
