@@ -61,3 +61,12 @@ def test_batch_setup_rejects_mixed_dim_or_k_without_gpu():
     arr = (st.StParams * 1)(st.params(si.base_params()))
     assert lib.st_batch_setup(arr, 0, None, ctypes.byref(b)) == st.ST_EINVAL
     assert lib.st_batch_destroy(None) == st.ST_OK
+
+
+def test_binding_refuses_the_pressure_space_it_does_not_implement():
+    import paper_2603_28706_gb300 as st
+    import st_inputs as si
+    with pytest.raises(ValueError):
+        st.params(si.base_params(pressure_space=1))
+    P = st.params(si.base_params(gamma_cip=0.5, finest_patches=0))
+    assert P.gamma_cip == 0.5 and P.finest_patches == 0
