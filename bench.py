@@ -289,7 +289,7 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
             "W": work(n_l, n) if ok else None, "n_nl_mean": float(np.mean(n_nl)) if ok else None}
 
 
-def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate"):
+def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=None):
     """Analogue of the solver evaluation of Sec. 7 (Table newton-compact, eq.
     work, eq. perf-profile) on synthetic channel problems: every (p, delta,
     mesh) instance with Pic, exN and modN."""
@@ -305,6 +305,8 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate"):
                                      nu=1e-3, nu_inf=0.0, sigma_max=1e-4, inflow_profile=1, vbar=0.1,
                                      levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30,
                                      finest_patches=0 if patches == "surrogate" else 1)
+                if omega is not None:
+                    prm["omega"] = omega
                 row = {"cells": 4 * n * n, "p": pe, "delta": delta}
                 for v in SWEEP_VARIANTS:
                     row[v] = sweep_instance(st, torch, prm, tangents[v], SWEEP_SLABS, vprec)
@@ -313,6 +315,7 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate"):
     taus = [1.0, 1.25, 1.5, 2.0, 3.0, 5.0, 10.0]
     prof = perf_profile(W, taus)
     return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "finest_patches": patches,
+            "omega": omega if omega is not None else si.base_params(dim=2)["omega"],
             "meshes_cells": [4 * n * n for n in SWEEP_MESHES],
             "p": list(SWEEP_P),
             "delta": list(SWEEP_DELTA), "slabs": SWEEP_SLABS, "wall_s": time.perf_counter() - t0,
@@ -506,6 +509,7 @@ def main():
     ap.add_argument("--sweep-vcycle", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the sweep")
     ap.add_argument("--sweep-patches", default="surrogate", choices=["surrogate", "exact"],
                     help="finest-level Vanka patches of the sweep: the surrogate of eq. surrogate-diag or exact")
+    ap.add_argument("--sweep-omega", type=float, default=None, help="Vanka damping of the sweep (default: 2D default)")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     args = ap.parse_args()
@@ -529,7 +533,7 @@ def main():
         print(json.dumps(batched_comparison(st, torch)))
         return
     if args.sweep:
-        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches)))
+        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches, args.sweep_omega)))
         return
     stream = torch.cuda.current_stream()
     if args.cip_only:
