@@ -441,6 +441,17 @@ def replica_throughput(ms_local, dofs, applies, device="cpu"):
     return ms, ws * dofs * applies / (ms * 1e-3)
 
 
+def fp64_peak_tflops(torch, device):
+    """Derived FP64 peak: SMs x 2 FP64 FMA per clock x 2 flops x the maximum
+    SM clock (2070 MHz on GB300, the clock nvidia-smi reports as max).  The
+    SM count is read from the device."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    return sms * 2 * 2 * FP64_CLOCK_HZ / 1e12
+
+
+FP64_CLOCK_HZ = 2.070e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -587,7 +598,7 @@ def main():
     torch.cuda.synchronize()
     apply_ms = r0.elapsed_time(r1) / reps
     fl = flops_per_apply(p)
-    peak = 152 * 2 * 2 * 2.070e9 / 1e12  # TFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz
+    peak = fp64_peak_tflops(torch, local)
     achieved = fl / (apply_ms * 1e-3) / 1e12
     traffic, executed = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

@@ -207,7 +207,7 @@ const char* st_last_error(const st_problem* h);
  * device allocations, a latency-critical path that must not touch the
  * allocator).  It needs no handle: params gives the mesh, k and dt; r is an
  * FP64 finest-level slab vector (device pointer, caller-owned) and *out (host)
- * receives |r|_M, the block mass norm of Sec. 6.1.  The work vectors and
+ * receives |r|_M, the block mass norm computed by st_mnorm.  The work vectors and
  * partial sums live in a static device array of 16 MiB that every GPU loading
  * the library holds until exit, so the slab may have at most
  * (2^21 - 2048) / 2 = 1 047 552 dofs; larger slabs give ST_EINVAL with a

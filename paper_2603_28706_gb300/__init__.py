@@ -141,20 +141,39 @@ def _prec_dtype(prec):
     return torch.float64 if prec == ST_FP64 else torch.float32
 
 
+def slab_dofs(p):
+    """(k+1)(d (2nx+1)(2ny+1)(2nz+1) + (nx+1)(ny+1)(nz+1)): the length of a
+    finest-level slab vector for the parameter dict p (Q2/Q1, eq. slab-system)."""
+    d = p["dim"]
+    n = [p["nx"], p["ny"], p["nz"] if d == 3 else 0]
+    nq2 = nq1 = 1
+    for a in range(d):
+        nq2 *= 2 * n[a] + 1
+        nq1 *= n[a] + 1
+    return (p["k"] + 1) * (d * nq2 + nq1)
+
+
 def mnorm_noalloc(p, r, stream=None):
     """|r|_M without a handle and without any device allocation (st_mnorm_noalloc).
 
     For callers that cannot allocate device memory; the library keeps a static
     16 MiB scratch array per GPU, which limits the slab to 1 047 552 dofs.
-    Calls that overlap on the GPU share that array and must be serialised."""
+    Calls that overlap on the GPU share that array and must be serialised.
+    r must live on the current CUDA device (the one whose copy of the array
+    the call uses) and hold exactly slab_dofs(p) doubles."""
     import torch
     lib = load()
     P = params(p)
+    ptr = _ptr(r, torch.float64, slab_dofs(p), "r")
+    if r.device.index != torch.cuda.current_device():
+        raise ValueError("r is on cuda:%d but the current device is cuda:%d"
+                         % (r.device.index, torch.cuda.current_device()))
     if stream is None:
         stream = torch.cuda.current_stream()
+    elif stream.device.index != r.device.index:
+        raise ValueError("the stream is not on r's device")
     v = ctypes.c_double()
-    st = lib.st_mnorm_noalloc(ctypes.byref(P), ctypes.c_void_p(stream.cuda_stream),
-                              _ptr(r, torch.float64, None, "r"), ctypes.byref(v))
+    st = lib.st_mnorm_noalloc(ctypes.byref(P), ctypes.c_void_p(stream.cuda_stream), ptr, ctypes.byref(v))
     if st != ST_OK:
         raise StError(st, "st_mnorm_noalloc failed (see stderr)")
     return v.value

@@ -19,9 +19,28 @@ __global__ void cast_kernel(const A* __restrict__ x, B* __restrict__ y, size_t n
     y[i] = (B)x[i];
 }
 
+// multiprocessor count of the current device, read once per device
+int sm_count() {
+  static std::mutex mu;
+  static int cached[256] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// grid-stride launches: at most 16 CTAs of BT threads per SM
+size_t grid_cap() { return 16 * (size_t)sm_count(); }
+
 unsigned grid_for(size_t n) {
   size_t g = (n + BT - 1) / BT;
-  if (g > 152 * 16) g = 152 * 16;
+  const size_t cap = grid_cap();
+  if (g > cap) g = cap;
   return (unsigned)(g < 1 ? 1 : g);
 }
 
@@ -187,7 +206,7 @@ cudaError_t mass_apply(const st_problem* h, int level, const T* x, T* y, T* work
       const int cpn = part == 0 ? d : 1;
       const long total = npt * nblk;
       unsigned grid = (unsigned)((total + BT - 1) / BT);
-      if (grid > 152 * 16) grid = 152 * 16;
+      if (grid > grid_cap()) grid = (unsigned)grid_cap();
       if (part == 0)
         mass_pass<T, 2><<<grid, BT, 0, h->stream>>>(src, dst, g[0], g[1], g[2], dir, L.h[dir], nblk, sc, cpn,
                                                      (T)M[0], (T)M[1], (T)M[2], (T)M[4], (T)M[5], (T)M[8]);
@@ -358,7 +377,7 @@ extern "C" st_status st_mnorm_noalloc(const st_params* P, void* cuda_stream, con
       const int cpn = partv == 0 ? d : 1;
       const long total = npt * nblk;
       unsigned grid = (unsigned)((total + BT - 1) / BT);
-      if (grid > 152 * 16) grid = 152 * 16;
+      if (grid > grid_cap()) grid = (unsigned)grid_cap();
       if (partv == 0)
         mass_pass<double, 2><<<grid, BT, 0, stream>>>(src, dst, g[0], g[1], g[2], dir, hh[dir], nblk, sc, cpn, M[0],
                                                        M[1], M[2], M[4], M[5], M[8]);

@@ -191,3 +191,84 @@ def test_deterministic_repeat():
     a = prob.jacobian_apply(st.ST_MODN, dU).clone()
     b = prob.jacobian_apply(st.ST_MODN, dU)
     assert torch.equal(a, b)
+
+
+def _clip_state(p, a=3.0):
+    """u = (1 + 0.2 mu) (a y^2, 0 [, 0]) at every Radau node mu (exact in Q2),
+    pressure 0; returns the slab vector and the stress magnitudes
+    |sigma| = mu(A)|A| at every cell quadrature point (3-point Gauss per
+    direction; only y matters), with A = D u, |A|^2 = 2 (a y (1 + 0.2 mu))^2."""
+    s = oracle.sizes(p)
+    K1, d = p["k"] + 1, p["dim"]
+    ny, Ly = p["ny"], p["Ly"]
+    g2 = [2 * p["nx"] + 1, 2 * ny + 1, (2 * p["nz"] + 1) if d == 3 else 1]
+    y = (np.arange(g2[1]) * Ly / (2 * ny))
+    yy = np.broadcast_to(y[None, :, None], (g2[2], g2[1], g2[0])).reshape(-1)
+    U = np.zeros(s["Nst"])
+    gq = 0.5 + np.array([-1.0, 0.0, 1.0]) * np.sqrt(15.0) / 10.0  # Gauss-Legendre on [0, 1]
+    yq = ((np.arange(ny)[:, None] + gq[None, :]) * Ly / ny).reshape(-1)
+    sig = []
+    for mu in range(K1):
+        f = 1.0 + 0.2 * mu
+        U[mu * s["Mv"]: mu * s["Mv"] + s["Nq2"]] = f * a * yy ** 2
+        A = np.sqrt(2.0) * np.abs(f * a * yq)
+        sig.append(p["nu"] * (p["delta"] ** 2 + A ** 2) ** (0.5 * (p["p"] - 2.0)) * A)
+    return U, np.concatenate(sig)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_modn_clip_active_and_inactive(dim):
+    # a state whose stress magnitude at the quadrature points spans sigma_max:
+    # the clip s = min(1, sigma_max/|sigma|) of eq. local-tangent-clip is
+    # below 1 at some points and equal to 1 at others
+    p = si.base_params(dim=dim, nx=3, ny=6, nz=2, k=1, p=1.4, delta=1e-2, nu=0.5, nu_inf=0.01, gamma1=20.0,
+                       gamma2=10.0)
+    U, sig = _clip_state(p)
+    p["sigma_max"] = float(np.median(sig))
+    clipped = np.mean(sig > p["sigma_max"])
+    assert 0.2 <= clipped <= 0.8, clipped
+    dU = si.uniform_state(p, 5)
+    st = gpu()
+    prob = st.Problem(p)
+    J = {}
+    for tg, to in TANGENTS:
+        Jr = oracle.jacobian_apply(p, to, U, dU)
+        prob.linearize(tg, dev(U))
+        Jg = prob.jacobian_apply(tg, dev(dU))
+        assert relerr(Jg, Jr) <= TOL64, (tg, relerr(Jg, Jr))
+        J[to] = Jr
+    prob.close()
+    # the clip changes the tangent: modN lies strictly between Pic and exN
+    scale = np.abs(J[oracle.EXN]).max()
+    assert np.abs(J[oracle.MODN] - J[oracle.EXN]).max() > 1e3 * TOL64 * scale
+    assert np.abs(J[oracle.MODN] - J[oracle.PIC]).max() > 1e3 * TOL64 * scale
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_state_at_rest(dim):
+    # U = 0: A = 0 at every quadrature point, so sigma = 0 and the modN clip
+    # takes s = 0 (reading C5); all three tangents reduce to eta(0) Id.  The
+    # residual at rest carries only the data (v_prev, inflow lifting).
+    p = si.base_params(dim=dim, nx=3, ny=3, nz=2, k=1, p=1.3, delta=1e-3, nu=0.2, nu_inf=0.01, sigma_max=0.05,
+                       inflow_profile=1, gamma1=20.0, gamma2=10.0)
+    s = oracle.sizes(p)
+    U = np.zeros(s["Nst"])
+    dU = si.uniform_state(p, 9)
+    vp = si.uniform(s["Mv"], 10)
+    st = gpu()
+    prob = st.Problem(p)
+    Rr = oracle.residual(p, U, vprev=vp)
+    assert relerr(prob.residual(dev(U), dev(vp)), Rr) <= TOL64
+    J = []
+    for tg, to in TANGENTS:
+        Jr = oracle.jacobian_apply(p, to, U, dU)
+        prob.linearize(tg, dev(U))
+        Jg = prob.jacobian_apply(tg, dev(dU))
+        assert relerr(Jg, Jr) <= TOL64, (tg, relerr(Jg, Jr))
+        Jg32 = prob.jacobian_apply(tg, dev(dU, torch.float32), prec=st.ST_FP32)
+        assert relerr(Jg32, Jr) <= TOL32
+        J.append(Jg.cpu().numpy())
+    prob.close()
+    # at rest the convection vanishes and the tangents coincide
+    assert np.abs(J[0] - J[1]).max() <= 1e-13 * np.abs(J[1]).max()
+    assert np.abs(J[2] - J[1]).max() <= 1e-13 * np.abs(J[1]).max()
