@@ -94,6 +94,13 @@ typedef struct {
                                  surrogate-diag, Sec. 6.3); 1: exact patches
                                  R_K J_n R_K^T of the linearisation, under the same
                                  refresh rule (not with gamma_cip > 0)               */
+  int coarse_solve;           /* coarsest level of the V-cycle: 0 = coarse_sweeps
+                                 Vanka steps; 1 = FP64-accurate direct solve of the
+                                 Galerkin operator A_0 (dense FP64 assembly, FP32
+                                 Gauss-Jordan inverse, FP64 iterative refinement to
+                                 |b - A_0 x|_2 <= 1e-12 |b|_2, at most 10 steps);
+                                 needs a nonsingular A_0 (a Gamma_N side fixes the
+                                 pressure constant) of at most 20000 dofs          */
 } st_params;
 
 typedef struct {
@@ -181,7 +188,9 @@ st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, co
 
 /* d = B^{-1} r: one space-time multigrid V-cycle on the finest level
  * (Sec. 6.3): pre_smooth Vanka sweeps, restriction P^T, recursion, coarsest
- * solve, prolongation P, post_smooth sweeps.  r, d: finest slab vectors of
+ * solve (coarse_solve: Vanka steps, or the FP64-accurate direct solve; with
+ * levels = 1 the finest level is the coarsest), prolongation P, post_smooth
+ * sweeps.  r, d: finest slab vectors of
  * dtype prec (d is overwritten). */
 st_status st_vcycle(st_problem* h, st_prec prec, const void* r, void* d);
 

@@ -20,8 +20,10 @@ restatement on the oracle's assembled matrices, small meshes only:
   vcycle             pre-smoothing, restriction, recursion, coarsest-level
                      treatment, prolongation, post-smoothing
 Readings (the paper defers to its references here): the coarsest level is
-treated by `coarse_sweeps` additive Vanka steps with exact patches starting
-from zero; patches are cell patches; omega is a scalar.  With CIP (eq.
+either solved exactly (coarse_solve="direct": a sparse LU of the Galerkin
+operator A_0, the FP64-accurate coarse solve) or treated by `coarse_sweeps`
+additive Vanka steps with exact patches starting from zero
+(coarse_solve="sweeps"); patches are cell patches; omega is a scalar.  With CIP (eq.
 scip-def) the finest-level defects and the finest-level patches
 (R_K A R_K^T of the surrogate operator) include it, while the Galerkin coarse
 operators, and hence the coarse patches, are built from the cell-local part
@@ -29,6 +31,7 @@ of the Jacobian (everything but the interior-face CIP coupling).
 """
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spl
 
 from . import (EXN, MODN, PIC, T_ALL, assemble_csr, cell_dofs, gauss01, sizes,  # noqa: F401
                time_tables)
@@ -153,8 +156,13 @@ class Hierarchy:
     iterate; the finest-level surrogate patches are rebuilt only when asked
     (the refresh rule of Sec. 6.3 keeps them otherwise)."""
 
-    def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True):
+    def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True,
+                 coarse_solve="sweeps"):
+        if coarse_solve not in ("sweeps", "direct"):
+            raise ValueError("coarse_solve must be 'sweeps' or 'direct'")
         self.p, self.levels = p, levels
+        self.coarse_solve = coarse_solve
+        self.lu0 = None
         self.omega = omega
         self.pre, self.post, self.coarse_sweeps = pre, post, coarse_sweeps
         self.surrogate = surrogate
@@ -175,6 +183,8 @@ class Hierarchy:
         self.Afine = assemble_csr(self.p, var, U) if cip else self.A[L]
         for l in range(L, 0, -1):
             self.A[l - 1] = galerkin(self.A[l], self.P[l])
+        if self.coarse_solve == "direct":
+            self.lu0 = spl.splu(self.A[0].tocsc())
         for l in range(self.levels):
             if l == L and not rebuild_finest and self.Ainv[L] is not None:
                 continue
@@ -205,6 +215,8 @@ class Hierarchy:
             l = self.levels - 1
         d = np.zeros_like(r)
         if l == 0:
+            if self.lu0 is not None:
+                return self.lu0.solve(r)
             return self.smooth(0, r, d, self.coarse_sweeps)
         d = self.smooth(l, r, d, self.pre)
         rc = self.P[l].T @ (r - self.op(l) @ d)

@@ -3,8 +3,10 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "st_blas.cuh"
+#include "st_coarse.cuh"
 #include "st_internal.h"
 #include "st_face.cuh"
 #include "st_operator.cuh"
@@ -229,6 +231,20 @@ st_status check_params(const st_params& P, std::string& why) {
   if (P.nx % div || P.ny % div || (P.dim == 3 && P.nz % div))
     return why = "cell counts must be divisible by 2^(levels-1)", ST_EINVAL;
   if (P.inflow_profile != 0 && P.inflow_profile != 1) return why = "inflow_profile must be 0 or 1", ST_EINVAL;
+  if (P.coarse_solve != 0 && P.coarse_solve != 1) return why = "coarse_solve must be 0 or 1", ST_EINVAL;
+  if (P.coarse_solve == 1) {
+    long n2 = 1, n1 = 1;
+    const int nn[3] = {P.nx, P.ny, P.dim == 3 ? P.nz : 0};
+    for (int a = 0; a < P.dim; ++a) {
+      const long m = nn[a] / div;
+      n2 *= 2 * m + 1;
+      n1 *= m + 1;
+    }
+    const long n0 = (long)(P.k + 1) * (P.dim * n2 + n1);
+    if (n0 > COARSE_DIRECT_MAX)
+      return why = "coarse_solve = 1: the coarsest level has " + std::to_string(n0) + " dofs, the direct solve takes at most " +
+                   std::to_string(COARSE_DIRECT_MAX) + " (add levels)", ST_EINVAL;
+  }
   const long ncells = (long)P.nx * P.ny * (P.dim == 3 ? P.nz : 1);
   if (ncells > (1L << 30)) return why = "mesh too large", ST_EINVAL;
   return ST_OK;

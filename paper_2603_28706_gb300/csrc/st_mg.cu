@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "st_blas.cuh"
+#include "st_coarse.cuh"
 #include "st_internal.h"
 
 namespace st {
@@ -1194,6 +1195,7 @@ struct MgState {
   bool g_failed = false;         // capture failed for this key: eager
   bool c13 = false;              // finest surrogate patches diagonalised in time (TimeEig)
   TimeEig te;
+  CoarseDirect cd;               // direct solve of the coarsest level (coarse_solve = 1)
 };
 
 namespace {
@@ -1231,6 +1233,7 @@ void free_mg(MgState* m) {
   cudaFree(m->fcache_rep32);
   cudaFree(m->bcells);
   cudaFree(m->d_tab);
+  coarse_direct_free(m->cd);
   m->Erep = nullptr;
   m->Urep = nullptr;
   m->cache_rep64 = m->fcache_rep64 = nullptr;
@@ -1291,10 +1294,34 @@ cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
     e = cudaMalloc(&m->d_tab, sizeof(tab));
     if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess && h->P.coarse_solve == 1) e = coarse_direct_alloc(m->cd, h->lev[0].Nst);
   m->prec = prec;
   m->allocated = e == cudaSuccess;
   return e;
 }
+
+CoarseGeom coarse_geom(const st_problem* h) {
+  CoarseGeom g;
+  memset(&g, 0, sizeof(g));
+  const Level& L = h->lev[0];
+  g.dim = h->dim;
+  g.K1 = h->K1;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = L.n[d];
+    g.g2[d] = L.g2[d];
+    g.g1[d] = L.g1[d];
+    for (int i = 0; i < 9; ++i) g.M1h[d][i] = h->R.M1[i] * (d < h->dim ? L.h[d] : 1.0);
+  }
+  g.Nq2 = L.Nq2;
+  g.Mv = L.Mv;
+  g.Mp = L.Mp;
+  for (int i = 0; i < h->K1 * h->K1; ++i) g.Kt[i] = h->T.Kt[i];
+  return g;
+}
+
+// refinement steps and relative tolerance of the coarsest-level direct solve
+constexpr int COARSE_REFINE_STEPS = 10;
+constexpr double COARSE_RTOL = 1e-12;
 
 PatchArgs patch_args(const st_problem* h, int level, bool surrogate) {
   PatchArgs pa;
@@ -1452,7 +1479,10 @@ cudaError_t vcycle_rec(st_problem* h, MgState* m, int l, const T* r, T* d) {
   const Level& L = h->lev[l];
   cudaError_t e = cudaMemsetAsync(d, 0, L.Nst * sizeof(T), h->stream);
   if (e != cudaSuccess) return e;
-  if (l == 0) return vanka_steps<T>(h, m, 0, h->P.coarse_sweeps, r, d);
+  if (l == 0)
+    return h->P.coarse_solve == 1
+               ? coarse_direct_solve<T>(m->cd, r, d, COARSE_REFINE_STEPS, COARSE_RTOL, h->nsm, h->stream)
+               : vanka_steps<T>(h, m, 0, h->P.coarse_sweeps, r, d);
   e = vanka_steps<T>(h, m, l, h->P.pre_smooth, r, d);
   if (e != cudaSuccess) return e;
   MgLevelData& D = m->L[l];
@@ -1510,7 +1540,8 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
   // finest level: exact element matrices per node (for the Galerkin operators
   // and the exact finest patches)
   const bool exact_finest = h->P.finest_patches == 1;
-  if (nl > 1 || exact_finest)
+  const bool direct = h->P.coarse_solve == 1;
+  if (nl > 1 || exact_finest || direct)
     for (int mu = 0; mu < K1 && e == cudaSuccess; ++mu)
       e = prec == ST_FP64 ? elm_dispatch<double>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc)
                           : elm_dispatch<float>(h, L, prec, tangent, cache, fcache, mu, K1, mu, m->L[L].E, m->bcells, m->nbc);
@@ -1576,8 +1607,15 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup Galerkin");
-  // patches: assemble + factorise
+  // the coarsest level's direct solve: dense A_0 and its inverse
   e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess && direct) {
+    const CoarseGeom cg = coarse_geom(h);
+    e = prec == ST_FP64 ? coarse_direct_setup<double>(cg, (const double*)m->L[0].E, m->cd, h->d_err, h->nsm, h->stream)
+                        : coarse_direct_setup<float>(cg, (const float*)m->L[0].E, m->cd, h->d_err, h->nsm, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup coarse direct solve");
+  // patches: assemble + factorise (the error flag also carries the coarse inversion's zero pivots)
   for (int l = 0; l < nl && e == cudaSuccess; ++l) {
     const Level& Lv = h->lev[l];
     const bool sur = (l == L) && !exact_finest;
@@ -1649,7 +1687,8 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
   e = cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_check(h, e, "st_precond_setup");
-  if (flag) return set_error(h, ST_SINGULAR_PATCH, "st_precond_setup: a patch matrix has a zero pivot");
+  if (flag) return set_error(h, ST_SINGULAR_PATCH, "st_precond_setup: a patch matrix (or the coarsest-level matrix) "
+                                                   "has a zero pivot");
   h->precond_valid = true;
   h->precond_prec = prec;
   return ST_OK;

@@ -150,3 +150,63 @@ def test_vcycle_exact_finest_patches(case):
         d = prob.vcycle(dev(r, dt), prec=prec)
         assert rel(d, ref) <= tol, (prec, rel(d, ref))
     prob.close()
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=4, ny=3, k=1), dict(dim=2, nx=3, ny=3, k=2, inflow_profile=1),
+                                  dict(dim=3, nx=2, ny=2, nz=2, k=1), dict(dim=3, nx=3, ny=2, nz=2, k=1,
+                                                                           inflow_profile=1, Lx=2.0)])
+def test_coarse_direct_solve_is_exact(case):
+    # levels = 1 and no smoothing: the V-cycle is the coarsest-level direct
+    # solve of the whole slab operator J_n (coarse_solve = 1), FP64-accurate
+    # (dense FP64 assembly, FP32 inverse, FP64 refinement to 1e-12); the
+    # oracle solves the assembled matrix with a sparse LU
+    import scipy.sparse.linalg as spl
+    p = si.base_params(p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, gamma1=20.0, gamma2=10.0, levels=1,
+                       pre_smooth=0, post_smooth=0, coarse_solve=1, **case)
+    st = gpu()
+    U = smooth_state(p)
+    r = si.uniform(oracle.sizes(p)["Nst"], 3)
+    for tg in (1, 2):
+        A = oracle.assemble_csr(p, VAR[tg], U)
+        ref = spl.spsolve(A.tocsc(), r)
+        prob = st.Problem(p)
+        prob.linearize(tg, dev(U))
+        d = prob.vcycle(dev(r), prec=st.ST_FP64)
+        assert rel(d, ref) <= 1e-10, (tg, rel(d, ref))
+        d32 = prob.vcycle(dev(r, torch.float32), prec=st.ST_FP32)
+        assert rel(d32, ref) <= TOL32, (tg, rel(d32, ref))
+        prob.close()
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=8, ny=4, k=1, levels=3, inflow_profile=1),
+                                  dict(dim=3, nx=4, ny=4, nz=4, k=1, levels=2),
+                                  dict(dim=3, nx=4, ny=2, nz=2, k=2, levels=2)])
+def test_vcycle_coarse_direct(case):
+    # the V-cycle with the direct coarsest-level solve against the oracle
+    # hierarchy with a sparse LU at level 0
+    p = si.base_params(p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, coarse_solve=1, **case)
+    st = gpu()
+    U = smooth_state(p)
+    r = si.uniform(oracle.sizes(p)["Nst"], 1)
+    H = mg.Hierarchy(p, VAR[2], U, p["levels"], p["omega"], p["pre_smooth"], p["post_smooth"],
+                     coarse_solve="direct")
+    ref = H.vcycle(r)
+    Hs = mg.Hierarchy(p, VAR[2], U, p["levels"], p["omega"], p["pre_smooth"], p["post_smooth"], coarse_sweeps=1)
+    assert np.abs(Hs.vcycle(r) - ref).max() > 1e-6 * np.abs(ref).max()  # the coarse treatment matters
+    prob = st.Problem(p)
+    prob.linearize(2, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        outs = []
+        for _ in range(3):  # eager, captured, replayed: the refinement loop is graph-safe
+            d = prob.vcycle(dev(r, dt), prec=prec)
+            assert rel(d, ref) <= tol, (prec, rel(d, ref))
+            outs.append(d.clone())
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2]), prec
+    prob.close()
+
+
+def test_coarse_direct_rejects_large_coarsest_level():
+    st = gpu()
+    p = si.base_params(dim=3, nx=16, ny=16, nz=16, k=1, levels=1, coarse_solve=1)
+    with pytest.raises(st.StError):
+        st.Problem(p)

@@ -122,3 +122,21 @@ def test_newton_variants_converge_to_one_solution():
     # exact Newton: the last contractions are faster than linear (q-superlinear)
     q = h[1:] / h[:-1]
     assert q[-1] < 0.1 * q[0] or h[-1] < 1e-12 * h[0]
+
+
+def test_direct_coarse_correction_is_galerkin_orthogonal():
+    # two levels, no smoothing, exact coarsest solve: d = P A_0^{-1} P^T r with
+    # A_0 = P^T A P, so the restricted residual P^T (r - A d) vanishes; one
+    # level: the V-cycle is A^{-1} r itself
+    p = si.base_params(dim=2, nx=4, ny=4, k=1, p=1.5, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.1)
+    U = si.fourier_state(p, 0)
+    s = oracle.sizes(p)
+    r = si.uniform(s["Nst"], 4)
+    A = oracle.assemble_csr(p, oracle.MODN, U)
+    H = mg.Hierarchy(p, oracle.MODN, U, 2, 0.2, 0, 0, coarse_solve="direct")
+    d = H.vcycle(r)
+    P = H.P[1]
+    assert np.abs(P.T @ (r - A @ d)).max() <= 1e-10 * np.abs(P.T @ r).max()
+    assert np.abs(r - A @ d).max() > 1e-3 * np.abs(r).max()  # a coarse correction, not a solve
+    H1 = mg.Hierarchy(p, oracle.MODN, U, 1, 0.2, 0, 0, coarse_solve="direct")
+    assert np.abs(A @ H1.vcycle(r) - r).max() <= 1e-10 * np.abs(r).max()
