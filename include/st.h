@@ -194,6 +194,23 @@ st_status st_vanka_smooth(st_problem* h, int level, int sweeps, st_prec prec, co
  * dtype prec (d is overwritten). */
 st_status st_vcycle(st_problem* h, st_prec prec, const void* r, void* d);
 
+typedef struct {
+  int iters;                  /* FGMRES iterations                                   */
+  double res_norm;            /* |b - J x|_M at exit                                 */
+  double rhs_norm;            /* |b|_M                                               */
+} st_linsolve_info;
+
+/* x = J^{-1} b for the current linearisation (st_linearize): right-
+ * preconditioned FGMRES(fgmres_restart) in FP64 in the block mass inner
+ * product of Sec. 6.1 (classical Gram-Schmidt twice), one V-cycle of
+ * precision vcycle_prec per iteration (Sec. 6.3), from x = 0 until
+ * |b - J x|_M <= rtol |b|_M or maxit iterations.  Builds the preconditioner
+ * when it is missing or of the other precision.  b, x: FP64 finest slab
+ * vectors.  Synchronous.  info may be NULL.  ST_NOT_CONVERGED when maxit is
+ * reached first (x then holds the last iterate). */
+st_status st_fgmres_solve(st_problem* h, st_prec vcycle_prec, const void* b, void* x, double rtol, int maxit,
+                          st_linsolve_info* info);
+
 /* Globalised (modified) Newton on the slab (Sec. 4.1, 6.1-6.3):
  *   repeat: R = R_n(U); stop if |R|_M <= tol_abs or <= tol_rel |R^0|_M
  *   (eq. nk-stop); linearise with `tangent`; refresh the preconditioner by the

@@ -20,7 +20,7 @@ STATUS = {0: "ST_OK", 1: "ST_EINVAL", 2: "ST_ECUDA", 3: "ST_ENOMEM", 4: "ST_NOT_
 
 EXPORTED = ["st_setup_mesh", "st_destroy", "st_num_dofs", "st_residual", "st_linearize", "st_jacobian_apply",
             "st_mnorm", "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step", "st_last_error",
-            "st_mnorm_noalloc", "st_batch_setup", "st_batch_destroy", "st_batch_num_dofs", "st_batch_linearize",
+            "st_mnorm_noalloc", "st_fgmres_solve", "st_batch_setup", "st_batch_destroy", "st_batch_num_dofs", "st_batch_linearize",
             "st_batch_jacobian_apply", "st_batch_residual", "st_batch_newton_step", "st_batch_last_error"]
 
 
@@ -48,6 +48,10 @@ class StNewtonInfo(ctypes.Structure):
                 ("fgmres_iters_last", ctypes.c_int), ("patch_rebuilds", ctypes.c_int),
                 ("lambda_last", ctypes.c_double), ("res_norm_initial", ctypes.c_double),
                 ("res_norm_final", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class StLinsolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("res_norm", ctypes.c_double), ("rhs_norm", ctypes.c_double)]
 
 
 class StError(RuntimeError):
@@ -86,6 +90,8 @@ def load(build_if_missing=True):
     lib.st_vanka_smooth.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.st_vcycle.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.st_newton_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(StNewtonInfo)]
+    lib.st_fgmres_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(StLinsolveInfo)]
     lib.st_last_error.argtypes = [vp]
     lib.st_last_error.restype = ctypes.c_char_p
     lib.st_mnorm_noalloc.argtypes = [P, vp, vp, ctypes.POINTER(ctypes.c_double)]
@@ -107,7 +113,7 @@ def load(build_if_missing=True):
     for name in EXPORTED:
         getattr(lib, name)
     for name in ("st_setup_mesh", "st_destroy", "st_residual", "st_linearize", "st_jacobian_apply", "st_mnorm",
-                 "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step"):
+                 "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step", "st_fgmres_solve"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -286,6 +292,18 @@ class Problem:
             d = torch.empty(n, dtype=dt, device=r.device)
         self._check(self.lib.st_vcycle(self.h, prec, _ptr(r, dt, n, "r"), _ptr(d, dt, n, "d")), "st_vcycle")
         return d
+
+    def fgmres_solve(self, b, x=None, rtol=1e-8, maxit=200, vcycle_prec=ST_FP32, raise_on_fail=True):
+        import torch
+        n = self.num_dofs()
+        if x is None:
+            x = torch.empty(n, dtype=torch.float64, device=b.device)
+        info = StLinsolveInfo()
+        st = self.lib.st_fgmres_solve(self.h, vcycle_prec, _ptr(b, torch.float64, n, "b"),
+                                      _ptr(x, torch.float64, n, "x"), float(rtol), int(maxit), ctypes.byref(info))
+        if raise_on_fail and st != ST_OK:
+            raise StError(st, "st_fgmres_solve: %s" % self.lib.st_last_error(self.h).decode())
+        return st, x, {name: getattr(info, name) for name, _ in StLinsolveInfo._fields_}
 
     def newton_step(self, tangent, U, v_prev, f=None, vcycle_prec=ST_FP32, raise_on_fail=True):
         import torch

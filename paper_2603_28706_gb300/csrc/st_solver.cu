@@ -237,6 +237,37 @@ void krylov_destroy(st_problem* h) {
 
 using namespace st;
 
+extern "C" st_status st_fgmres_solve(st_problem* h, st_prec vcycle_prec, const void* b, void* x, double rtol,
+                                     int maxit, st_linsolve_info* info) {
+  if (!h) return ST_EINVAL;
+  if (!b || !x) return set_error(h, ST_EINVAL, "st_fgmres_solve: b and x are required");
+  if (vcycle_prec != ST_FP64 && vcycle_prec != ST_FP32) return set_error(h, ST_EINVAL, "st_fgmres_solve: bad precision");
+  if (!(rtol > 0.0) || maxit < 1) return set_error(h, ST_EINVAL, "st_fgmres_solve: need rtol > 0 and maxit >= 1");
+  if (!h->lin_valid) return set_error(h, ST_EINVAL, "st_fgmres_solve: no linearisation (call st_linearize)");
+  KrylovWs* k = nullptr;
+  cudaError_t e = get_ws(h, k);
+  if (e != cudaSuccess) return cuda_check(h, e, "st_fgmres_solve workspace");
+  if (!h->precond_valid || h->precond_prec != vcycle_prec) {
+    st_status s = mg_setup(h, vcycle_prec, true);
+    if (s != ST_OK) return s;
+  }
+  int its = 0;
+  double lres = 0.0, bn = 0.0;
+  st_status st = fgmres(h, k, vcycle_prec, (const double*)b, rtol, maxit, its, lres, bn);
+  if (st != ST_OK) return st;
+  e = cudaMemcpyAsync(x, k->x, k->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_check(h, e, "st_fgmres_solve");
+  if (info) {
+    info->iters = its;
+    info->res_norm = lres;
+    info->rhs_norm = bn;
+  }
+  if (lres > rtol * bn * (1.0 + 1e-12))
+    return set_error(h, ST_NOT_CONVERGED, "st_fgmres_solve: maxit reached before the tolerance");
+  return ST_OK;
+}
+
 extern "C" st_status st_newton_step(st_problem* h, st_tangent tangent, st_prec vcycle_prec, void* U,
                                     const void* v_prev, const void* f, st_newton_info* info) {
   if (!h) return ST_EINVAL;

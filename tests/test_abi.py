@@ -41,7 +41,8 @@ def test_setup_rejects_bad_parameters_without_gpu():
     lib = st.load()
     h = ctypes.c_void_p()
     for bad in (dict(dim=4), dict(p=2.5), dict(k=7), dict(levels=3, nx=6), dict(delta=0.0), dict(nx=0),
-                dict(gamma_cip=-1.0), dict(finest_patches=2), dict(finest_patches=1, gamma_cip=1.0)):
+                dict(gamma_cip=-1.0), dict(finest_patches=2), dict(finest_patches=1, gamma_cip=1.0),
+                dict(coarse_solve=2), dict(coarse_solve=1, nx=16, ny=16, nz=16, levels=1)):
         P = st.params(si.base_params(**bad))
         assert lib.st_setup_mesh(ctypes.byref(P), None, ctypes.byref(h)) == st.ST_EINVAL
     assert lib.st_setup_mesh(None, None, ctypes.byref(h)) == st.ST_EINVAL

@@ -120,3 +120,49 @@ def test_newton_exact_finest_patches_matches_oracle():
         err = np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max()
         assert err <= 1e-8, (prec, err, ginfo, info["iters"])
     prob.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("coarse", [0, 1])
+def test_fgmres_solve_matches_sparse_solve(dim, coarse):
+    # st_fgmres_solve: J x = b to a relative M-norm residual of 1e-10 with the
+    # V-cycle (Vanka or direct coarsest solve), against a sparse LU of the
+    # oracle's assembled Jacobian
+    import scipy.sparse.linalg as spl
+    st = gpu()
+    p = dict(problem(dim), coarse_solve=coarse)
+    U0, _ = start(p)
+    s = oracle.sizes(p)
+    b = si.uniform(s["Nst"], 11)
+    A = oracle.assemble_csr(p, oracle.MODN, U0)
+    x_ref = spl.spsolve(A.tocsc(), b)
+    prob = st.Problem(p)
+    prob.linearize(st.ST_MODN, dev(U0))
+    for prec in (st.ST_FP64, st.ST_FP32):
+        status, x, info = prob.fgmres_solve(dev(b), rtol=1e-10, maxit=200, vcycle_prec=prec)
+        assert status == st.ST_OK
+        assert info["res_norm"] <= 1e-10 * info["rhs_norm"] * (1 + 1e-9)
+        assert abs(info["rhs_norm"] - np.sqrt(oracle.mnorm2(p, b))) <= 1e-12 * info["rhs_norm"]
+        err = np.abs(x.cpu().numpy() - x_ref).max() / np.abs(x_ref).max()
+        assert err <= 1e-6, (prec, err, info)
+    # a budget of one iteration misses the tolerance and says so
+    status, x, info = prob.fgmres_solve(dev(b), rtol=1e-10, maxit=1, raise_on_fail=False)
+    assert status == st.ST_NOT_CONVERGED and info["iters"] == 1
+    prob.close()
+
+
+def test_newton_with_direct_coarse_solve_matches_oracle():
+    st = gpu()
+    p = dict(problem(3), coarse_solve=1)
+    U0, vprev = start(p)
+    Uo, info = kr.newton(p, oracle.MODN, U0, vprev, vcycle_levels=p["levels"], max_iter=40, tol_rel=p["tol_rel"],
+                         tol_abs=p["tol_abs"], omega=p["omega"], coarse_solve="direct")
+    assert info["status"] == "ok"
+    prob = st.Problem(p)
+    for prec in (st.ST_FP64, st.ST_FP32):
+        U = dev(U0)
+        status, ginfo = prob.newton_step(2, U, dev(vprev), vcycle_prec=prec)
+        assert status == st.ST_OK, ginfo
+        err = np.abs(U.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+        assert err <= 1e-8, (prec, err, ginfo, info["iters"])
+    prob.close()
