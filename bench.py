@@ -700,7 +700,7 @@ def main():
     achieved = fl / (apply_ms * 1e-3) / 1e12
     traffic, executed = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "one modN apply: st_op_kernel<3,2,double,OP_JAC,1> (all cells, colour-private outputs) + st_face_kernel (side stream) + st_cbuf_sum + st_face_add", "traffic_source": os.path.relpath(PROFILE, ROOT),
+                "traffic": traffic, "kernel": "one modN apply: st_op_kernel<3,2,double,OP_JAC,1> (all cells, colour-private outputs) + st_face_kernel (side stream, overlapping the volume kernel) + st_cbuf_sum + st_face_add", "traffic_source": os.path.relpath(PROFILE, ROOT),
                 "apply_ms": apply_ms, "flops_per_apply": fl, "flop_per_dof": FLOP_PER_DOF,
                 "executed_fp64_flops_per_apply": executed,
                 "executed_frac": (executed / (apply_ms * 1e-3) / 1e12 / peak) if executed else None,
