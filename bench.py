@@ -219,22 +219,41 @@ def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300):
 BATCH_WORKLOAD = ("64 independent 3D unit-cube instances, n^3 hexes with n drawn from {8, 10, .., 32}, Q2/Q1, "
                   "dG(1), p ~ U[1.1, 1.9], delta = 10^U[-6, -2], nu=1e-3, nu_inf=1e-4, smooth random velocity "
                   "(8 Fourier modes, seed i); FP64 modN Jacobian apply of all instances in one persistent launch")
-BATCH_NEWTON_WORKLOAD = ("8 channel instances 4x1x1 from rest, 4n x n x n hexes with n in {4, 6, 8}, dG(1), p ~ U[1.5, 1.9], "
-                         "delta = 10^U[-3, -2]; one modN Newton step each to |R|_M <= 1e-8 |R0|_M, FP32 V-cycle "
-                         "(2 levels); concurrent (one thread and stream each) vs one after another")
+BATCH_STEP_WORKLOAD = ("the same 64 instances; one modN Newton step each: batched linearisation and residual "
+                       "(one persistent volume launch each), then J dU = R_n(U) by FP64 FGMRES(50) to relative 1e-8 "
+                       "(at most 200 iterations) with the FP32 V-cycle (levels down to an odd or 2-cell coarsest "
+                       "level, FP64-accurate direct coarsest solve where it has at most 20000 dofs, else 8 Vanka "
+                       "sweeps), all instances concurrent (one host thread and stream each); v_prev = last node "
+                       "+ 0.1 uniform noise")
 
 
-def batched_comparison(st, torch):
-    """Throughput of the batched operator (st_batch_jacobian_apply: one
-    persistent volume launch over all instances) against the same applies
-    issued instance by instance, and the concurrent batched Newton step
-    against sequential single Newton steps."""
-    rng = np.random.default_rng(0)
+def batch_instances(rng):
     plist = []
     for i in range(64):
         n = 2 * int(rng.integers(4, 17))
         plist.append(si.base_params(dim=3, nx=n, ny=n, nz=n, k=1, dt=0.01, p=float(rng.uniform(1.1, 1.9)),
                                     delta=float(10 ** rng.uniform(-6, -2)), nu=1e-3, nu_inf=1e-4, sigma_max=1e-3))
+    return plist
+
+
+def hierarchy_for(p):
+    """Levels down to an odd or 2-cell coarsest mesh; the direct coarsest
+    solve where that level has at most 20000 dofs."""
+    n, levels = p["nx"], 1
+    while n % 2 == 0 and n > 2:
+        n //= 2
+        levels += 1
+    n0 = (p["k"] + 1) * (3 * (2 * n + 1) ** 3 + (n + 1) ** 3)
+    return dict(p, levels=levels, coarse_solve=1 if n0 <= 20000 else 0, coarse_sweeps=8)
+
+
+def batched_comparison(st, torch, step=True):
+    """Throughput of the batched operator (st_batch_jacobian_apply: one
+    persistent volume launch over all instances) against the same applies
+    issued instance by instance, and one modN Newton step of every instance
+    (batched linearisation and residual, concurrent FGMRES solves)."""
+    rng = np.random.default_rng(0)
+    plist = batch_instances(rng)
     b = st.Batch(plist)
     U = [torch.from_numpy(si.fourier_state(p, i)).cuda() for i, p in enumerate(plist)]
     dU = [torch.from_numpy(si.uniform_state(p, 100 + i)).cuda() for i, p in enumerate(plist)]
@@ -266,43 +285,40 @@ def batched_comparison(st, torch):
     for sp in singles:
         sp.close()
     b.close()
-    del U, dU, out_b, out_s
+    del dU, out_b, out_s
     torch.cuda.empty_cache()
     res = {"workload": BATCH_WORKLOAD, "instances": len(plist), "dofs": ndofs, "batched_ms": tb,
            "one_by_one_ms": ts, "batched_dofs_per_s": ndofs / (tb * 1e-3),
            "one_by_one_dofs_per_s": ndofs / (ts * 1e-3), "bitwise_equal": same}
-    # Newton: concurrent instances vs one after another
-    nl = []
-    for i in range(8):
-        nx = 8 * int(rng.integers(2, 5))
-        nl.append(si.config(5, nx=nx, ny=nx // 4, nz=nx // 4, levels=2, p=float(rng.uniform(1.5, 1.9)),
-                            delta=float(10 ** rng.uniform(-3, -2)), tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=4,
-                            newton_maxit=30))
-    b = st.Batch(nl)
-    n_i = [b.num_dofs(i) for i in range(len(nl))]
-    v_i = [b.velocity_size(i) for i in range(len(nl))]
-    Ub = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in n_i]
-    vp = [torch.zeros(v, dtype=torch.float64, device="cuda") for v in v_i]
+    if not step:
+        return res
+    # one Newton step per instance, as one batch
+    hl = [hierarchy_for(p) for p in plist]
+    b = st.Batch(hl)
+    vp = []
+    for i, (p, u) in enumerate(zip(hl, U)):
+        mv = si.sizes(p)["Mv"]
+        vp.append(u[p["k"] * mv:(p["k"] + 1) * mv].clone() + 0.1 * torch.from_numpy(si.uniform(mv, 200 + i)).cuda())
+    R = [torch.empty_like(u) for u in U]
+    xs = [torch.empty_like(u) for u in U]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    status_b, infos = b.newton_step(st.ST_MODN, Ub, vp, vcycle_prec=st.ST_FP32, raise_on_fail=False)
+    b.linearize(st.ST_MODN, U)
+    b.residual(U, vp, Rs=R)
+    status, xs, infos = b.fgmres_solve(R, xs, rtol=1e-8, maxit=200, vcycle_prec=st.ST_FP32, raise_on_fail=False)
     torch.cuda.synchronize()
-    tcb = time.perf_counter() - t0
+    tstep = time.perf_counter() - t0
+    conv = [inf["res_norm"] <= 1e-8 * inf["rhs_norm"] * (1 + 1e-12) for inf in infos]
+    res["newton_step"] = {
+        "workload": BATCH_STEP_WORKLOAD, "seconds": tstep, "dofs": ndofs, "dofs_per_s": ndofs / tstep,
+        "converged": int(sum(conv)), "instances": len(hl),
+        "per_instance": [{"n": p["nx"], "p": round(p["p"], 3), "delta": float("%.3g" % p["delta"]),
+                          "levels": p["levels"], "coarse_solve": p["coarse_solve"], "fgmres_iters": inf["iters"],
+                          "rel_residual": inf["res_norm"] / max(inf["rhs_norm"], 1e-300), "converged": c}
+                         for p, inf, c in zip(hl, infos, conv)]}
     b.close()
-    tseq, ok_seq = 0.0, True
-    for i, p in enumerate(nl):
-        sp = st.Problem(p)
-        Us = torch.zeros(n_i[i], dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s1, _ = sp.newton_step(st.ST_MODN, Us, vp[i], vcycle_prec=st.ST_FP32, raise_on_fail=False)
-        torch.cuda.synchronize()
-        tseq += time.perf_counter() - t0
-        ok_seq = ok_seq and s1 == st.ST_OK and torch.equal(Us, Ub[i])
-        sp.close()
-    res["newton"] = {"workload": BATCH_NEWTON_WORKLOAD, "concurrent_s": tcb, "one_by_one_s": tseq,
-                     "status": int(status_b), "newton_iters": [x["newton_iters"] for x in infos],
-                     "same_result_as_single": bool(ok_seq)}
+    del U, vp, R, xs
+    torch.cuda.empty_cache()
     return res
 
 
@@ -639,7 +655,9 @@ def main():
         print(json.dumps(config3_solve(st, torch, args.config3_mesh, args.config3_levels, args.config3_coarse)))
         return
     if args.batched_only:
-        print(json.dumps(batched_comparison(st, torch)))
+        res = batched_comparison(st, torch)
+        res["autotune"] = st.autotune_report().splitlines()
+        print(json.dumps(res))
         return
     if args.sweep:
         print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches, args.sweep_omega)))
@@ -782,6 +800,7 @@ def main():
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roofline, "fp32_apply": roofline32, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
                 "cip": cip, "newton": newton, "batched": batched,
+                "autotune": st.autotune_report().splitlines(),
                 "clocks": clk.summary()}
         print(json.dumps(line))
     prob.close()

@@ -227,6 +227,18 @@ st_status st_newton_step(st_problem* h, st_tangent tangent, st_prec vcycle_prec,
 /* Message describing the last failure on h (never NULL). */
 const char* st_last_error(const st_problem* h);
 
+/* Launch shapes chosen by the library's autotuner in this process, one line
+ * per tuned kernel and launch size: the choice and every candidate's time.
+ * The first launch of the Jacobian action's volume kernel (cells per CTA),
+ * of the Vanka patch solves and of the coarse-level operator (threads per
+ * CTA, CTAs per SM) with a new size times the candidates on the real
+ * arguments with CUDA events (not while the stream is being captured; not at
+ * all when the environment sets ST_AUTOTUNE=0) and keeps the fastest; every
+ * candidate computes the same values.  Writes at most len bytes (NUL-
+ * terminated) into buf (may be NULL) and returns the length the whole report
+ * needs, NUL included. */
+size_t st_autotune_report(char* buf, size_t len);
+
 /* Allocation-free variant of st_mnorm.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (a memory
  * pool owned by another framework with a hard cap, a plugin host that forbids
@@ -280,6 +292,16 @@ st_status st_batch_residual(st_batch* b, st_prec prec, const void* const* U, con
  * (the others still complete). */
 st_status st_batch_newton_step(st_batch* b, st_tangent tangent, st_prec vcycle_prec, void* const* U,
                                const void* const* v_prev, const void* const* f, st_newton_info* info);
+/* st_fgmres_solve for every instance (after st_batch_linearize), the
+ * instances driven concurrently (one host thread and one internal CUDA stream
+ * each): x[i] = J_i^{-1} rhs[i] to |rhs[i] - J_i x[i]|_M <= rtol |rhs[i]|_M
+ * with one V-cycle of precision vcycle_prec per iteration.  info[i] filled
+ * (info may be NULL).  Synchronous.  Returns ST_OK when every instance met
+ * rtol, else the status of the first instance that did not (the others still
+ * complete). */
+st_status st_batch_fgmres_solve(st_batch* b, st_prec vcycle_prec, const void* const* rhs, void* const* x,
+                                double rtol, int maxit, st_linsolve_info* info);
+
 /* Message describing the last failure on b (never NULL). */
 const char* st_batch_last_error(const st_batch* b);
 

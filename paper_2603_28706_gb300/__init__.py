@@ -21,7 +21,8 @@ STATUS = {0: "ST_OK", 1: "ST_EINVAL", 2: "ST_ECUDA", 3: "ST_ENOMEM", 4: "ST_NOT_
 EXPORTED = ["st_setup_mesh", "st_destroy", "st_num_dofs", "st_residual", "st_linearize", "st_jacobian_apply",
             "st_mnorm", "st_precond_setup", "st_vanka_smooth", "st_vcycle", "st_newton_step", "st_last_error",
             "st_mnorm_noalloc", "st_fgmres_solve", "st_batch_setup", "st_batch_destroy", "st_batch_num_dofs", "st_batch_linearize",
-            "st_batch_jacobian_apply", "st_batch_residual", "st_batch_newton_step", "st_batch_last_error"]
+            "st_batch_jacobian_apply", "st_batch_residual", "st_batch_newton_step", "st_batch_last_error",
+            "st_autotune_report", "st_batch_fgmres_solve"]
 
 
 class StParams(ctypes.Structure):
@@ -105,6 +106,11 @@ def load(build_if_missing=True):
     lib.st_batch_jacobian_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, vpp, vpp]
     lib.st_batch_residual.argtypes = [vp, ctypes.c_int, vpp, vpp, vpp, vpp]
     lib.st_batch_newton_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, vpp, vpp, vpp, ctypes.POINTER(StNewtonInfo)]
+    lib.st_batch_fgmres_solve.argtypes = [vp, ctypes.c_int, vpp, vpp, ctypes.c_double, ctypes.c_int,
+                                          ctypes.POINTER(StLinsolveInfo)]
+    lib.st_batch_fgmres_solve.restype = ctypes.c_int
+    lib.st_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.st_autotune_report.restype = ctypes.c_size_t
     lib.st_batch_last_error.argtypes = [vp]
     lib.st_batch_last_error.restype = ctypes.c_char_p
     for name in ("st_batch_setup", "st_batch_destroy", "st_batch_linearize", "st_batch_jacobian_apply",
@@ -184,6 +190,15 @@ def mnorm_noalloc(p, r, stream=None):
     if st != ST_OK:
         raise StError(st, "st_mnorm_noalloc failed (see stderr)")
     return v.value
+
+
+def autotune_report():
+    """The launch shapes the library's autotuner chose in this process (st_autotune_report)."""
+    lib = load()
+    n = lib.st_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(int(n))
+    lib.st_autotune_report(buf, n)
+    return buf.value.decode()
 
 
 class Problem:
@@ -407,6 +422,18 @@ class Batch:
                                                _ptr_array(v_prevs, dt, vs, "v_prev"), fa,
                                                _ptr_array(Rs, dt, sz, "R")), "st_batch_residual")
         return Rs
+
+    def fgmres_solve(self, rhs, xs=None, rtol=1e-8, maxit=200, vcycle_prec=ST_FP32, raise_on_fail=True):
+        import torch
+        sz = [self.num_dofs(i) for i in range(self.n)]
+        if xs is None:
+            xs = [torch.empty(sz[i], dtype=torch.float64, device=rhs[i].device) for i in range(self.n)]
+        infos = (StLinsolveInfo * self.n)()
+        st = self.lib.st_batch_fgmres_solve(self.b, vcycle_prec, _ptr_array(rhs, torch.float64, sz, "rhs"),
+                                            _ptr_array(xs, torch.float64, sz, "x"), float(rtol), int(maxit), infos)
+        if raise_on_fail and st != ST_OK:
+            raise StError(st, "st_batch_fgmres_solve: %s" % self.lib.st_batch_last_error(self.b).decode())
+        return st, xs, [{name: getattr(infos[i], name) for name, _ in StLinsolveInfo._fields_} for i in range(self.n)]
 
     def newton_step(self, tangent, Us, v_prevs, fs=None, vcycle_prec=ST_FP32, raise_on_fail=True):
         import torch

@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libst.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-CU = ["st_api.cu", "st_blas.cu", "st_op2d.cu", "st_op3d.cu", "st_mg.cu", "st_coarse.cu", "st_solver.cu", "st_batch.cu"]
+CU = ["st_api.cu", "st_blas.cu", "st_op2d.cu", "st_op3d.cu", "st_mg.cu", "st_coarse.cu", "st_solver.cu", "st_batch.cu", "st_tune.cu"]
 CPP = ["st_tables.cpp"]
 
 

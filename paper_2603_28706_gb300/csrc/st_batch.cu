@@ -233,6 +233,35 @@ st_status st_batch_newton_step(st_batch* b, st_tangent tangent, st_prec vcycle_p
   return ST_OK;
 }
 
+st_status st_batch_fgmres_solve(st_batch* b, st_prec vcycle_prec, const void* const* rhs, void* const* x,
+                                double rtol, int maxit, st_linsolve_info* info) {
+  if (!b) return ST_EINVAL;
+  if (!rhs || !x) return batch_error(b, ST_EINVAL, "st_batch_fgmres_solve: rhs and x are required");
+  const int n = (int)b->inst.size();
+  for (int i = 0; i < n; ++i)
+    if (!rhs[i] || !x[i])
+      return batch_error(b, ST_EINVAL, "st_batch_fgmres_solve: a NULL vector for instance " + std::to_string(i));
+  cudaError_t e = fork_instances(b);  // the instances see the caller's earlier work
+  if (e != cudaSuccess) return batch_cuda(b, e, "st_batch_fgmres_solve");
+  std::vector<st_status> res(n, ST_OK);
+  std::vector<st_linsolve_info> loc(n);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(b->dev);
+      res[i] = st_fgmres_solve(b->inst[i], vcycle_prec, rhs[i], x[i], rtol, maxit, info ? &info[i] : &loc[i]);
+    });
+  for (auto& t : th) t.join();
+  e = join_instances(b);
+  if (e != cudaSuccess) return batch_cuda(b, e, "st_batch_fgmres_solve");
+  for (int i = 0; i < n; ++i)
+    if (res[i] != ST_OK)
+      return batch_error(b, res[i], "st_batch_fgmres_solve: instance " + std::to_string(i) + ": " +
+                                        st_last_error(b->inst[i]));
+  return ST_OK;
+}
+
 const char* st_batch_last_error(const st_batch* b) {
   if (!b) return "null batch";
   return b->last_error.c_str();

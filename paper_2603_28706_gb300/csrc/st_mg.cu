@@ -25,6 +25,7 @@
 #include "st_blas.cuh"
 #include "st_coarse.cuh"
 #include "st_internal.h"
+#include "st_tune.h"
 
 namespace st {
 
@@ -1151,6 +1152,10 @@ __global__ void rep_state_kernel(const double* __restrict__ U, double* __restric
   }
 }
 
+std::string shape_label(const LaunchShape& c, int nsm) {
+  return std::to_string(c.threads) + " threads x " + std::to_string(c.grid / (nsm > 0 ? nsm : 1)) + "/SM";
+}
+
 unsigned gridn(size_t n, int nsm) {
   size_t g = (n + 255) / 256;
   const size_t cap = 16 * (size_t)nsm;
@@ -1371,14 +1376,23 @@ cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
   PatchArgs pa = patch_args(h, l, false);
   const ColourMap cm = colour_map(h, L);
   T* cb = (T*)m->L[l].cbuf;
-  const unsigned g = (unsigned)(L.ncells < 8L * h->nsm ? L.ncells : 8L * h->nsm);
-  if (h->dim == 2)
-    coarse_apply<2, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm, L.ncells, L.Nq2,
-                                                 L.Nq1, L.Mv, L.Mp);
-  else
-    coarse_apply<3, T><<<g, 128, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm, L.ncells, L.Nq2,
-                                                 L.Nq1, L.Mv, L.Mp);
-  cudaError_t e = cudaGetLastError();
+  // autotuned launch shape (threads per CTA, CTAs per SM); one CTA per cell at a time
+  const LaunchShape cand[4] = {{128, 8L * h->nsm}, {256, 8L * h->nsm}, {128, 16L * h->nsm}, {256, 4L * h->nsm}};
+  auto run = [&](int i) {
+    const unsigned g = (unsigned)(L.ncells < cand[i].grid ? L.ncells : cand[i].grid);
+    if (h->dim == 2)
+      coarse_apply<2, T><<<g, cand[i].threads, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm,
+                                                               L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+    else
+      coarse_apply<3, T><<<g, cand[i].threads, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm,
+                                                               L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+    return cudaGetLastError();
+  };
+  const int pick = tune_pick(
+      "coarse_apply<" + std::to_string(h->dim) + "," + (sizeof(T) == 8 ? "double" : "float") + "> K1=" +
+          std::to_string(h->K1) + " cells=" + std::to_string(L.ncells),
+      4, run, [&](int i) { return shape_label(cand[i], h->nsm); }, h->stream);
+  cudaError_t e = run(pick);
   if (e != cudaSuccess) return e;
   colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, y, L.Nst, (T)1, 0);
   return cudaGetLastError();
@@ -1395,32 +1409,47 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
     sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // all patches in one launch into the colour buffers, then d += omega sum
+    // all patches in one launch into the colour buffers, then d += omega sum;
+    // the launch shape (threads per patch CTA, CTAs per SM) is autotuned
     const ColourMap cm = colour_map(h, L);
     T* cb = (T*)D.cbuf;
-    const unsigned g = (unsigned)(L.ncells < 16L * h->nsm ? L.ncells : 16L * h->nsm);
-    const int nt = N <= 128 ? 128 : 256;
-    if (m->c13 && l == (int)h->lev.size() - 1) {
-      VankaC13 vc;
+    const int nt0 = N <= 128 ? 128 : 256;
+    const LaunchShape cand[5] = {{nt0, 16L * h->nsm}, {128, 16L * h->nsm}, {256, 8L * h->nsm},
+                                 {512, 4L * h->nsm}, {128, 32L * h->nsm}};
+    const bool c13 = m->c13 && l == (int)h->lev.size() - 1;
+    VankaC13 vc;
+    memset(&vc, 0, sizeof(vc));
+    if (c13) {
       vc.nb = m->te.nb;
       memcpy(vc.tin, m->te.tin, sizeof(vc.tin));
       memcpy(vc.tout, m->te.tout, sizeof(vc.tout));
-      if (h->dim == 2)
-        vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
-                                                             L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv,
-                                                             L.Mp);
-      else
-        vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
-                                                             L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv,
-                                                             L.Mp);
-    } else if (h->dim == 2) {
-      vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
-                                                       L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
-    } else {
-      vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
-                                                       L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
     }
-    e = cudaGetLastError();
+    auto run = [&](int i) {
+      const unsigned g = (unsigned)(L.ncells < cand[i].grid ? L.ncells : cand[i].grid);
+      const int nt = cand[i].threads;
+      if (c13) {
+        if (h->dim == 2)
+          vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+                                                               L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1,
+                                                               L.Mv, L.Mp);
+        else
+          vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+                                                               L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1,
+                                                               L.Mv, L.Mp);
+      } else if (h->dim == 2) {
+        vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+      } else {
+        vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+      }
+      return cudaGetLastError();
+    };
+    const int pick = tune_pick(std::string(c13 ? "vanka_patch_solve_c13<" : "vanka_patch_solve<") +
+                                   std::to_string(h->dim) + "," + (sizeof(T) == 8 ? "double" : "float") +
+                                   "> N=" + std::to_string(N) + " cells=" + std::to_string(L.ncells),
+                               5, run, [&](int i) { return shape_label(cand[i], h->nsm); }, h->stream);
+    e = run(pick);
     if (e != cudaSuccess) return e;
     colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, d, L.Nst, (T)h->P.omega, 1);
     e = cudaGetLastError();

@@ -6,6 +6,7 @@
 #include "st_cip.cuh"
 #include "st_face.cuh"
 #include "st_operator.cuh"
+#include "st_tune.h"
 
 namespace st {
 
@@ -127,13 +128,32 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   if (e != cudaSuccess) return e;
   set_volume_args<T>(h, L, a);
   {
-    // every resident CTA slot gets an equal share of the cells when there are
-    // at least half a batch per slot; smaller meshes use full batches
+    // Default: every resident CTA slot gets an equal share of the cells when
+    // there are at least half a batch per slot; smaller meshes use full
+    // batches.  The Jacobian action (the hot call) autotunes the number of
+    // cells per CTA: the balanced share of one, two or four CTA waves, or one
+    // batch of C cells per CTA (each CTA always runs batches of C cells).
     const long cap = (long)occ * h->nsm;
-    long grid = (L.ncells + Cfg::C - 1) / Cfg::C;
+    const long full = (L.ncells + Cfg::C - 1) / Cfg::C;
+    long grid = full;
     if (L.ncells >= cap * (Cfg::C / 2)) grid = cap;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
+    if (MODE == OP_JAC) {
+      long cand[4] = {grid, 2 * cap, 4 * cap, full};
+      for (long& c : cand) c = c < 1 ? 1 : (c > full ? full : c);
+      const std::string key = "st_op_kernel<" + std::to_string(DIM) + "," + std::to_string(K1) + "," +
+                              (sizeof(T) == 8 ? "double" : "float") + ",OP_JAC," + std::to_string(TAN) +
+                              "> cells=" + std::to_string(L.ncells);
+      const int pick = tune_pick(
+          key, 4,
+          [&](int i) {
+            kern<<<(unsigned)cand[i], Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
+            return cudaGetLastError();
+          },
+          [&](int i) { return "cells/CTA=" + std::to_string((L.ncells + cand[i] - 1) / cand[i]); }, h->stream);
+      grid = cand[pick];
+    }
     kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

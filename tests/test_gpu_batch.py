@@ -108,3 +108,47 @@ def test_batch_newton_matches_single():
             assert torch.equal(Ub[i], Us), (prec, i, (Ub[i] - Us).abs().max().item())
             prob.close()
     b.close()
+
+
+def test_batch_fgmres_solve_matches_single_solves():
+    # st_batch_fgmres_solve: every instance's linear solve (concurrent host
+    # threads and streams) gives the single-problem st_fgmres_solve result
+    st = gpu()
+    plist = [dict(p, levels=2 if all(p[a] % 2 == 0 for a in ("nx", "ny", "nz")) else 1, coarse_sweeps=4)
+             for p in instances(3)]
+    U = [si.fourier_state(p, 40 + i) for i, p in enumerate(plist)]
+    rhs = [si.uniform(oracle.sizes(p)["Nst"], 50 + i) for i, p in enumerate(plist)]
+    b = st.Batch(plist)
+    b.linearize(st.ST_MODN, [dev(u) for u in U])
+    status, xs, infos = b.fgmres_solve([dev(r) for r in rhs], rtol=1e-9, maxit=300)
+    assert status == st.ST_OK
+    for i, p in enumerate(plist):
+        assert infos[i]["res_norm"] <= 1e-9 * infos[i]["rhs_norm"] * (1 + 1e-9)
+        sp = st.Problem(p)
+        sp.linearize(st.ST_MODN, dev(U[i]))
+        s1, x1, inf1 = sp.fgmres_solve(dev(rhs[i]), rtol=1e-9, maxit=300)
+        assert s1 == st.ST_OK and inf1["iters"] == infos[i]["iters"]
+        assert torch.equal(x1, xs[i]), i
+        sp.close()
+    b.close()
+
+
+def test_autotuned_launch_shapes_do_not_change_results(monkeypatch):
+    # the autotuner times candidate launch shapes at the first launch of a
+    # new size; every candidate computes the same values, so the tuned apply
+    # equals the untuned default bit for bit, and the report names the choice
+    st = gpu()
+    p = si.base_params(dim=3, nx=7, ny=9, nz=5, k=1, p=1.4, delta=0.05, nu=0.3, nu_inf=0.01, sigma_max=0.05)
+    U = dev(si.uniform_state(p, 60))
+    dU = dev(si.uniform_state(p, 61))
+    prob = st.Problem(p)
+    prob.linearize(st.ST_MODN, U)
+    monkeypatch.setenv("ST_AUTOTUNE", "0")
+    ref = prob.jacobian_apply(st.ST_MODN, dU).clone()
+    monkeypatch.setenv("ST_AUTOTUNE", "1")
+    tuned = prob.jacobian_apply(st.ST_MODN, dU).clone()
+    again = prob.jacobian_apply(st.ST_MODN, dU)
+    assert torch.equal(ref, tuned) and torch.equal(tuned, again)
+    rep = st.autotune_report()
+    assert "cells=%d" % (7 * 9 * 5) in rep and "cells/CTA=" in rep, rep
+    prob.close()
