@@ -18,7 +18,8 @@
  *     U = [V_1 ... V_{k+1} | P_1 ... P_{k+1}]            (eq. slab-system)
  * V_mu is component-major (component c = 0..dim-1), each component
  * lexicographic on the Q2 node grid (2nx+1)(2ny+1)(2nz+1), x fastest;
- * P_mu is lexicographic on the Q1 grid (nx+1)(ny+1)(nz+1).  A velocity field
+ * P_mu is lexicographic on the Q1 grid (nx+1)(ny+1)(nz+1) (pressure_space = 1:
+ * (dim+1) coefficients per cell, cells lexicographic).  A velocity field
  * (v_prev, one time node) is dim*(2nx+1)(2ny+1)(2nz+1) values.  On level l
  * of the multigrid hierarchy the mesh is n/2^(L-l) cells per direction.
  *
@@ -101,6 +102,11 @@ typedef struct {
                                  |b - A_0 x|_2 <= 1e-12 |b|_2, at most 10 steps);
                                  needs a nonsingular A_0 (a Gamma_N side fixes the
                                  pressure constant) of at most 20000 dofs          */
+  int pressure_space;         /* 0: Q1 continuous pressure (Taylor-Hood); 1: P1disc,
+                                 the pair of the paper's experiments (Sec. 7): per
+                                 cell the basis 1, 2 r_a - 1 (r_a the cell's
+                                 reference coordinates), P_mu = [cell][1 + dim]
+                                 with cells lexicographic, x fastest                */
 } st_params;
 
 typedef struct {

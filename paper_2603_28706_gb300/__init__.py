@@ -41,7 +41,7 @@ class StParams(ctypes.Structure):
                 ("ew_gamma", ctypes.c_double), ("ew_alpha", ctypes.c_double), ("ew_max", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("lambda_min", ctypes.c_double),
                 ("coarse_sweeps", ctypes.c_int), ("gamma_cip", ctypes.c_double), ("finest_patches", ctypes.c_int),
-                ("coarse_solve", ctypes.c_int)]
+                ("coarse_solve", ctypes.c_int), ("pressure_space", ctypes.c_int)]
 
 
 class StNewtonInfo(ctypes.Structure):
@@ -125,12 +125,10 @@ def load(build_if_missing=True):
     return lib
 
 
-_OPTIONAL = {"gamma_cip": 0.0, "finest_patches": 0, "coarse_solve": 0}
+_OPTIONAL = {"gamma_cip": 0.0, "finest_patches": 0, "coarse_solve": 0, "pressure_space": 0}
 
 
 def params(p):
-    if p.get("pressure_space", 0) != 0:
-        raise ValueError("the CUDA library implements the Q2/Q1 pair only (pressure_space = 0)")
     return StParams(*[p.get(name, _OPTIONAL[name]) if name in _OPTIONAL else p[name] for name, _ in StParams._fields_])
 
 
@@ -175,6 +173,8 @@ def mnorm_noalloc(p, r, stream=None):
     r must live on the current CUDA device (the one whose copy of the array
     the call uses) and hold exactly slab_dofs(p) doubles."""
     import torch
+    if p.get("pressure_space", 0) != 0:
+        raise ValueError("st_mnorm_noalloc implements the Q2/Q1 pair only (pressure_space = 0)")
     lib = load()
     P = params(p)
     ptr = _ptr(r, torch.float64, slab_dofs(p), "r")

@@ -105,6 +105,7 @@ void make_level(const st_params& P, int nx, int ny, int nz, Level& L) {
     L.Nq1 *= L.g1[a];
     L.ncells *= L.n[a];
   }
+  if (P.pressure_space == 1) L.Nq1 = L.ncells * (d + 1);  // P1disc: 1 + dim coefficients per cell
   L.Mv = d * L.Nq2;
   L.Mp = L.Nq1;
   L.Nst = (long)(P.k + 1) * (L.Mv + L.Mp);
@@ -178,12 +179,22 @@ cudaError_t build_gather(const st_problem* h, Level& L, const std::vector<int>& 
           for (int x = 0; x < 2; ++x) {
             const int m3[3] = {x, y, z};
             if (m3[ax] != up) continue;
-            const long gp = (e3[0] + x) + L.g1[0] * ((e3[1] + y) + L.g1[1] * (e3[2] + z));
             GatherEnt g;
             g.fid = fid;
             g.tn = m3[t1] + 2 * (d == 3 ? m3[t2] : 0);
-            g.e = g.ed = 0.0;
-            pres[gp].push_back(g);
+            g.ed = 0.0;
+            if (h->P.pressure_space == 1) {
+              // P1disc: the face-vertex test reaches every coefficient j of the cell with weight T[m][j]
+              const int mc = x + 2 * y + 4 * z;
+              for (int j = 0; j <= d; ++j) {
+                g.e = pdisc_T(mc, j);
+                pres[cell * (d + 1) + j].push_back(g);
+              }
+            } else {
+              const long gp = (e3[0] + x) + L.g1[0] * ((e3[1] + y) + L.g1[1] * (e3[2] + z));
+              g.e = 1.0;
+              pres[gp].push_back(g);
+            }
           }
     }
   }
@@ -232,6 +243,7 @@ st_status check_params(const st_params& P, std::string& why) {
     return why = "cell counts must be divisible by 2^(levels-1)", ST_EINVAL;
   if (P.inflow_profile != 0 && P.inflow_profile != 1) return why = "inflow_profile must be 0 or 1", ST_EINVAL;
   if (P.coarse_solve != 0 && P.coarse_solve != 1) return why = "coarse_solve must be 0 or 1", ST_EINVAL;
+  if (P.pressure_space != 0 && P.pressure_space != 1) return why = "pressure_space must be 0 or 1", ST_EINVAL;
   if (P.coarse_solve == 1) {
     long n2 = 1, n1 = 1;
     const int nn[3] = {P.nx, P.ny, P.dim == 3 ? P.nz : 0};
@@ -240,7 +252,9 @@ st_status check_params(const st_params& P, std::string& why) {
       n2 *= 2 * m + 1;
       n1 *= m + 1;
     }
-    const long n0 = (long)(P.k + 1) * (P.dim * n2 + n1);
+    long ncells0 = 1;
+    for (int a = 0; a < P.dim; ++a) ncells0 *= nn[a] / div;
+    const long n0 = (long)(P.k + 1) * (P.dim * n2 + (P.pressure_space == 1 ? ncells0 * (P.dim + 1) : n1));
     if (n0 > COARSE_DIRECT_MAX)
       return why = "coarse_solve = 1: the coarsest level has " + std::to_string(n0) + " dofs, the direct solve takes at most " +
                    std::to_string(COARSE_DIRECT_MAX) + " (add levels)", ST_EINVAL;
@@ -297,6 +311,7 @@ void fill_op_args(const st_problem* h, int level, OpArgs& a) {
   a.L[2] = P.dim == 3 ? P.Lz : 1.0;
   a.dmask = P.dirichlet_mask;
   a.inflow = P.inflow_profile;
+  a.pdisc = P.pressure_space == 1 ? 1 : 0;
   a.face_off = L.d_face_off;
   a.err = h->d_err;
   a.gcip = P.gamma_cip;

@@ -180,6 +180,19 @@ cudaError_t cast_f32_f64(const float* x, double* y, size_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// P1disc pressure mass (block diagonal): on a cell of volume |K| the basis
+// 1, 2 r_a - 1 is orthogonal with integrals |K| and |K|/3, so
+// y = tau w_mu |K| diag(1, 1/3, .., 1/3) x per cell and time node.
+template <typename T>
+__global__ void pdisc_mass(const T* __restrict__ x, T* __restrict__ y, long ncells, int nl, int K1,
+                           const double* __restrict__ bscale, double vol) {
+  const long per = ncells * nl, total = per * K1;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int mu = (int)(i / per), j = (int)((i % per) % nl);
+    y[i] = (T)(bscale[mu] * vol * (j == 0 ? 1.0 : 1.0 / 3.0) * (double)x[i]);
+  }
+}
+
 template <typename T>
 cudaError_t mass_apply(const st_problem* h, int level, const T* x, T* y, T* work) {
   const Level& L = h->lev[level];
@@ -194,6 +207,15 @@ cudaError_t mass_apply(const st_problem* h, int level, const T* x, T* y, T* work
   T* t2 = work + L.Nst;
   // velocity: K1*d blocks of Nq2 on the Q2 grid; pressure: K1 blocks on the Q1 grid
   for (int part = 0; part < 2; ++part) {
+    if (part == 1 && h->P.pressure_space == 1) {
+      const size_t off = (size_t)K1 * L.Mv;
+      const double vol = L.h[0] * L.h[1] * (d == 3 ? L.h[2] : 1.0);
+      pdisc_mass<T><<<grid_for((size_t)K1 * L.Mp), BT, 0, h->stream>>>(x + off, y + off, L.ncells, d + 1, K1, bs,
+                                                                        vol);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     const long* g = part == 0 ? L.g2 : L.g1;
     const long npt = g[0] * g[1] * g[2];
     const int nblk = part == 0 ? K1 * d : K1;
@@ -304,7 +326,7 @@ extern "C" st_status st_mnorm_noalloc(const st_params* P, void* cuda_stream, con
   if (!P) return ST_EINVAL;
   const int d = P->dim;
   if ((d != 2 && d != 3) || P->nx < 1 || P->ny < 1 || (d == 3 && P->nz < 1) || P->k < 0 || P->k >= MAX_K1 ||
-      !(P->dt > 0) || !(P->Lx > 0) || !(P->Ly > 0) || (d == 3 && !(P->Lz > 0))) {
+      !(P->dt > 0) || !(P->Lx > 0) || !(P->Ly > 0) || (d == 3 && !(P->Lz > 0)) || P->pressure_space != 0) {
     fprintf(stderr, "st_mnorm_noalloc: invalid parameters\n");
     return ST_EINVAL;
   }

@@ -50,17 +50,35 @@ __global__ void __launch_bounds__(256) coarse_dense_add(const T* __restrict__ E,
              g.g2[0] * ((2L * ey + (q / 3) % 3) + g.g2[1] * (2L * ez + q / 9));
       } else {
         const int mm = loc - NC * NQ;
-        gi = (long)K1 * g.Mv + (long)mu * g.Mp + (ex + (mm & 1)) +
-             g.g1[0] * ((ey + ((mm >> 1) & 1)) + g.g1[1] * (ez + (mm >> 2)));
+        if (g.pdisc)  // the cell's coefficients; local pressure dofs beyond them are unused
+          gi = mm <= DIM ? (long)K1 * g.Mv + (long)mu * g.Mp + cell * (DIM + 1) + mm : -1;
+        else
+          gi = (long)K1 * g.Mv + (long)mu * g.Mp + (ex + (mm & 1)) +
+               g.g1[0] * ((ey + ((mm >> 1) & 1)) + g.g1[1] * (ez + (mm >> 2)));
       }
       sg[r] = gi;
     }
     __syncthreads();
     for (long t = threadIdx.x; t < (long)N * N; t += blockDim.x) {
       const int rr = (int)(t / N), cc = (int)(t % N);
+      if (sg[rr] < 0 || sg[cc] < 0) continue;
       const int mu = rr / NE, i = rr % NE, nu = cc / NE, j = cc % NE;
       double v = 0.0;
-      if (mu == nu) v = (double)E[((cell * K1 + mu) * NE + i) * (long)NE + j];
+      constexpr int NV = NC * NQ;
+      if (mu == nu) {
+        const T* Em = E + (cell * K1 + mu) * (long)NE * NE;
+        if (g.pdisc && i >= NV && j >= NV) {
+          for (int m = 0; m < NP; ++m)
+            for (int m2 = 0; m2 < NP; ++m2)
+              v += pdisc_T(m, i - NV) * (double)Em[(NV + m) * NE + NV + m2] * pdisc_T(m2, j - NV);
+        } else if (g.pdisc && i >= NV) {
+          for (int m = 0; m < NP; ++m) v += pdisc_T(m, i - NV) * (double)Em[(NV + m) * NE + j];
+        } else if (g.pdisc && j >= NV) {
+          for (int m = 0; m < NP; ++m) v += (double)Em[i * NE + NV + m] * pdisc_T(m, j - NV);
+        } else {
+          v = (double)Em[i * NE + j];
+        }
+      }
       if (i < NC * NQ && j < NC * NQ && i / NQ == j / NQ) v += g.Kt[mu * K1 + nu] * smass[(i % NQ) * NQ + (j % NQ)];
       A[sg[rr] * n + sg[cc]] += v;
     }

@@ -48,6 +48,7 @@ void coarse_direct_free(CoarseDirect& cd);
 // Geometry of the coarsest level for the dense assembly.
 struct CoarseGeom {
   int dim, K1;
+  int pdisc;          // P1disc pressure (element matrices in vertex form, see pdisc_T)
   int n[3];
   long g2[3], g1[3];
   long Nq2, Mv, Mp;

@@ -330,8 +330,18 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
         const int mx = ax == 0 ? up : (t1 == 0 ? q1 : 0);
         const int my = ax == 1 ? up : (t1 == 1 ? q1 : (t2 == 1 ? q2 : 0));
         const int mz = ax == 2 ? up : (t2 == 2 ? q2 : 0);
-        const long gp = (e3[0] + mx) + a.g1[0] * ((e3[1] + my) + a.g1[1] * (e3[2] + mz));
-        w[Cfg::oFP + m] = in[(long)K1 * a.Mv + (long)mu * a.Mp + gp];
+        if (a.pdisc) {
+          // P1disc: the cell's affine pressure at this face vertex (pdisc_T)
+          const int mc = mx + 2 * my + 4 * mz;
+          const T* pc = in + (long)K1 * a.Mv + (long)mu * a.Mp + (long)cell * (DIM + 1);
+          T v = pc[0];
+#pragma unroll
+          for (int j = 1; j <= DIM; ++j) v += ((mc >> (j - 1)) & 1) ? pc[j] : -pc[j];
+          w[Cfg::oFP + m] = v;
+        } else {
+          const long gp = (e3[0] + mx) + a.g1[0] * ((e3[1] + my) + a.g1[1] * (e3[2] + mz));
+          w[Cfg::oFP + m] = in[(long)K1 * a.Mv + (long)mu * a.Mp + gp];
+        }
       }
     }
     __syncthreads();
@@ -440,7 +450,8 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
 struct GatherEnt {
   int fid;    // boundary face
   int tn;     // face-plane node (velocity) or face pressure node (pressure)
-  double e;   // weight of the face value output
+  double e;   // weight of the face value output (pressure: of the face pressure test;
+              // 1 for Q1, T[m][j] of pdisc_T for P1disc)
   double ed;  // weight of the face normal-derivative output
 };
 
@@ -496,7 +507,7 @@ __global__ void st_face_add(const OpArgs a, int nvel, int ntot, const int* __res
       T acc = 0;
       for (int j = b; j < e; ++j) {
         const GatherEnt ge = gent[j];
-        acc += fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
+        acc += (T)ge.e * fscr[((long)ge.fid * K1 + mu) * NOUT + 2 * NC * NFQ + ge.tn];
       }
       out[(long)K1 * a.Mv + (long)mu * a.Mp + gnode[row]] += acc;
     }

@@ -78,6 +78,7 @@ struct OpArgs {
   double L[3];
   unsigned dmask;
   int inflow;
+  int pdisc;               // P1disc pressure: (DIM+1) cell coefficients, see pdisc_T
   int tangent;
   // data
   const void* in;          // dU (Jacobian) or U (residual, linearise)
@@ -104,6 +105,18 @@ struct OpArgs {
 };
 
 enum OpMode { OP_LIN = 0, OP_JAC = 1, OP_RES = 2, OP_ELM = 3 };
+
+// P1disc pressure (pressure_space = 1).  On a cell the pressure is
+// c_0 + sum_a c_{1+a} (2 r_a - 1), an affine function, so it lies in Q1 and
+// its values at the cell's vertices m = (m_0, m_1, m_2) (bit a of m: m_a) are
+// sum_j T[m][j] c_j with T[m][0] = 1, T[m][1+a] = 2 m_a - 1.  The kernels keep
+// the pressure in this vertex form (element matrices, sum-factorised passes)
+// and change basis where they meet slab vectors: values v = T c on input,
+// tests T^T t on output.  Global index of coefficient j of cell `cell` in the
+// pressure block of one time node: cell * (DIM + 1) + j.
+__host__ __device__ __forceinline__ double pdisc_T(int m, int j) {
+  return j == 0 ? 1.0 : (((m >> (j - 1)) & 1) ? 1.0 : -1.0);
+}
 
 // device scratch of a batched launch (st_batch.cu)
 struct BatchDev {

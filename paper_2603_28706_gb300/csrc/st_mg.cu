@@ -98,6 +98,57 @@ __global__ void restrict_pass(const T* __restrict__ x, T* __restrict__ y, int gi
   }
 }
 
+// P1disc pressure transfers, cell by cell.  A child with offset o in {0,1}^d
+// inside its parent holds the parent's affine pressure exactly: with the
+// basis 1, 2 r_a - 1 on both cells, r_parent = (r_child + o) / 2, so
+//   f_0 = c_0 + sum_a c_{1+a} (o_a - 1/2),   f_{1+a} = c_{1+a} / 2;
+// the restriction is the transpose (summed over the 2^d children).
+template <typename T, int DIM>
+__global__ void pdisc_prolong(const T* __restrict__ xc, T* __restrict__ yf, int nfx, int nfy, int nfz, int K1) {
+  const long ncf = (long)nfx * nfy * nfz, ncc = ncf >> DIM;
+  const int ncx = nfx / 2, ncy = nfy / 2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ncf * K1; t += (long)gridDim.x * blockDim.x) {
+    const int mu = (int)(t / ncf);
+    const long f = t % ncf;
+    const int fx = (int)(f % nfx), fy = (int)((f / nfx) % nfy), fz = (int)(f / ((long)nfx * nfy));
+    const long c = (fx >> 1) + (long)ncx * ((fy >> 1) + (long)ncy * (DIM == 3 ? (fz >> 1) : 0));
+    const int o[3] = {fx & 1, fy & 1, fz & 1};
+    const T* cc = xc + ((long)mu * ncc + c) * (DIM + 1);
+    T* ff = yf + ((long)mu * ncf + f) * (DIM + 1);
+    T v = cc[0];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) v += cc[1 + a] * (T)(o[a] - 0.5);
+    ff[0] = v;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ff[1 + a] = cc[1 + a] * (T)0.5;
+  }
+}
+
+template <typename T, int DIM>
+__global__ void pdisc_restrict(const T* __restrict__ xf, T* __restrict__ yc, int ncx, int ncy, int ncz, int K1) {
+  const long ncc = (long)ncx * ncy * ncz, ncf = ncc << DIM;
+  const int nfx = 2 * ncx, nfy = 2 * ncy;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < ncc * K1; t += (long)gridDim.x * blockDim.x) {
+    const int mu = (int)(t / ncc);
+    const long c = t % ncc;
+    const int cx = (int)(c % ncx), cy = (int)((c / ncx) % ncy), cz = (int)(c / ((long)ncx * ncy));
+    T acc[DIM + 1];
+#pragma unroll
+    for (int j = 0; j <= DIM; ++j) acc[j] = 0;
+    for (int ch = 0; ch < (1 << DIM); ++ch) {
+      const int o[3] = {ch & 1, (ch >> 1) & 1, (ch >> 2) & 1};
+      const long f = (2 * cx + o[0]) + (long)nfx * ((2 * cy + o[1]) + (long)nfy * (DIM == 3 ? 2 * cz + o[2] : 0));
+      const T* ff = xf + ((long)mu * ncf + f) * (DIM + 1);
+      acc[0] += ff[0];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) acc[1 + a] += ff[0] * (T)(o[a] - 0.5) + ff[1 + a] * (T)0.5;
+    }
+    T* cc = yc + ((long)mu * ncc + c) * (DIM + 1);
+#pragma unroll
+    for (int j = 0; j <= DIM; ++j) cc[j] = acc[j];
+  }
+}
+
 // ------------------------------------------------------------- Galerkin
 // E_c[cell][mu] = sum over the 2^d children of P_ch^T E_f[child][mu] P_ch, with
 // P_ch the child-local-dof <- parent-local-dof prolongation (block diagonal:
@@ -214,7 +265,46 @@ struct PatchArgs {
   int c13;             // surrogate patch diagonalised in time: nb complex blocks lambda_b M_v + S
   int nb;
   double lam[4][2];
+  int pdisc;           // P1disc pressure: patch pressure dofs are the cell's coefficients, the
+                       // element matrices' pressure part is in vertex form (pdisc_T)
 };
+
+// P1disc patch entry (row p, column q of a spatial block, one of them a
+// pressure dof): the cell's own element matrix with its pressure rows and
+// columns changed from vertex values to coefficients (T^T E T); local
+// pressure dofs beyond the DIM+1 coefficients are unused and get an
+// identity row, so the patch matrix stays invertible.  S[mu] as in
+// patch_assemble (surrogate: w_mu / w_0 times the representative matrix).
+template <int DIM, typename T>
+__device__ void pdisc_patch_entry(const T* __restrict__ E, int estride, const PatchArgs& pa, long K, int p, int q,
+                                  T* S) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP, NV = NC * NQ;
+  const bool pp = p >= NV, pq = q >= NV;
+  const int jp = p - NV, jq = q - NV;
+  if ((pp && jp > DIM) || (pq && jq > DIM)) {
+    for (int mu = 0; mu < pa.K1; ++mu) S[mu] = (p == q) ? (T)1 : (T)0;
+    return;
+  }
+  const int nmat = pa.surrogate ? 1 : pa.K1;
+  for (int s = 0; s < nmat; ++s) {
+    const T* Em = E + ((K * estride) + (pa.surrogate ? 0 : s)) * (long)NE * NE;
+    double v = 0.0;
+    if (pp && pq) {
+      for (int m = 0; m < NP; ++m)
+        for (int m2 = 0; m2 < NP; ++m2)
+          v += pdisc_T(m, jp) * (double)Em[(NV + m) * NE + NV + m2] * pdisc_T(m2, jq);
+    } else if (pp) {
+      for (int m = 0; m < NP; ++m) v += pdisc_T(m, jp) * (double)Em[(NV + m) * NE + q];
+    } else {
+      for (int m = 0; m < NP; ++m) v += (double)Em[p * NE + NV + m] * pdisc_T(m, jq);
+    }
+    if (pa.surrogate) {
+      for (int mu = 0; mu < pa.K1; ++mu) S[mu] = (T)(pa.wr[mu] * v);
+    } else {
+      S[s] = (T)v;
+    }
+  }
+}
 
 template <int DIM>
 __device__ __forceinline__ bool local_in(int dof, const int dl[3], int& out) {
@@ -269,7 +359,10 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
       // node index 0 / 1 in {-1, 0} / {0, 1}; the cells that do not are skipped
       // without their index arithmetic, in the same order as before
       int am[3] = {2, 2, 2};
-      {
+      if (pa.pdisc && (p >= NC * NQ || q >= NC * NQ)) {
+        pdisc_patch_entry<DIM, T>(E, estride, pa, K, p, q, S);
+        am[0] = am[1] = am[2] = 0;  // no neighbour sums: the pressure dofs belong to K alone
+      } else {
         int ip[3], iq[3];
         const bool vp = p < NC * NQ, vq = q < NC * NQ;
         const int np_ = vp ? p % NQ : p - NC * NQ, nq_ = vq ? q % NQ : q - NC * NQ;
@@ -917,7 +1010,7 @@ struct VankaC13 {
 template <int DIM, typename T>
 __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int K1, const T* __restrict__ defect,
                                       T* __restrict__ cb, long cstride, int n0, int n1, int n2, ColourMap cm,
-                                      long ncells, long Nq2, long Nq1, long Mv, long Mp) {
+                                      long ncells, long Nq2, long Nq1, long Mv, long Mp, int pdisc) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE, nb = vc.nb;
   __shared__ T sx[MAXN];
@@ -938,10 +1031,14 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
         g = (long)mu * Mv + c * Nq2 + (2L * ex + q % 3) + g2x * ((2L * ey + (q / 3) % 3) + g2y * (2L * ez + q / 9));
       } else {
         const int m = loc - NC * NQ;
-        g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+        if (pdisc) {  // the cell's P1disc coefficients; patch dofs beyond them are unused
+          g = m <= DIM ? (long)K1 * Mv + (long)mu * Mp + cell * (DIM + 1) + m : -1;
+        } else {
+          g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+        }
       }
       sg[r] = g;
-      sx[r] = defect[g];
+      sx[r] = g >= 0 ? defect[g] : (T)0;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nb * NE; t += blockDim.x) {
@@ -987,7 +1084,7 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
       const int mu = r / NE, p = r % NE;
       T x = 0;
       for (int b = 0; b < nb; ++b) x += (T)vc.tout[b][mu][0] * sz[b][p][0] - (T)vc.tout[b][mu][1] * sz[b][p][1];
-      ob[sg[r]] = x;
+      if (sg[r] >= 0) ob[sg[r]] = x;
     }
     __syncthreads();
   }
@@ -1012,7 +1109,7 @@ cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm,
 template <int DIM, typename T>
 __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __restrict__ defect, T* __restrict__ cb,
                                   long cstride, int n0, int n1, int n2, ColourMap cm, long ncells, long Nq2, long Nq1,
-                                  long Mv, long Mp) {
+                                  long Mv, long Mp, int pdisc) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE;
   __shared__ T sx[MAXN];
@@ -1032,17 +1129,21 @@ __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __re
         g = (long)mu * Mv + c * Nq2 + (2L * ex + q % 3) + g2x * ((2L * ey + (q / 3) % 3) + g2y * (2L * ez + q / 9));
       } else {
         const int m = loc - NC * NQ;
-        g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+        if (pdisc) {  // the cell's P1disc coefficients; patch dofs beyond them are unused
+          g = m <= DIM ? (long)K1 * Mv + (long)mu * Mp + cell * (DIM + 1) + m : -1;
+        } else {
+          g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
+        }
       }
       sg[r] = g;
-      sx[r] = defect[g];
+      sx[r] = g >= 0 ? defect[g] : (T)0;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
       T acc = 0;
 #pragma unroll 8
       for (int j = 0; j < N; ++j) acc = fma(A[(long)j * N + r], sx[j], acc);
-      ob[sg[r]] = acc;
+      if (sg[r] >= 0) ob[sg[r]] = acc;
     }
     __syncthreads();
   }
@@ -1061,6 +1162,7 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
   __shared__ long sg[MAXN];
   __shared__ T smass[NQ * NQ];             // velocity mass of one cell (tensor of the 1D masses)
   __shared__ T skt[MAX_K1][NC * NQ];       // sum_nu K_t[mu][nu] x_nu (velocity part)
+  __shared__ T sy[MAX_K1 * NP];            // P1disc: vertex-form pressure rows of the product
   const int N = K1 * NE;
   const int n0 = pa.n[0], n1 = pa.n[1];
   const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
@@ -1085,6 +1187,15 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
         g = (long)mu * Mv + c * Nq2 + (2L * ex + q % 3) + g2x * ((2L * ey + (q / 3) % 3) + g2y * (2L * ez + q / 9));
       } else {
         const int m = loc - NC * NQ;
+        if (pa.pdisc) {
+          // vertex value of the cell's affine pressure; the outputs are the coefficients' tests
+          const T* pc = x + (long)K1 * Mv + (long)mu * Mp + cell * (DIM + 1);
+          T v = pc[0];
+          for (int j = 1; j <= DIM; ++j) v += ((m >> (j - 1)) & 1) ? pc[j] : -pc[j];
+          sg[r] = -1;
+          sx[r] = v;
+          continue;
+        }
         g = (long)K1 * Mv + (long)mu * Mp + (ex + (m & 1)) + g1x * ((ey + ((m >> 1) & 1)) + g1y * (ez + (m >> 2)));
       }
       sg[r] = g;
@@ -1117,7 +1228,19 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
       }
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (act && hl == 0) ob[sg[r]] = acc;
+      if (act && hl == 0) {
+        if (sg[r] >= 0) ob[sg[r]] = acc;
+        else sy[mu * NP + (i - NC * NQ)] = acc;
+      }
+    }
+    if (pa.pdisc) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < K1 * (DIM + 1); t += blockDim.x) {
+        const int mu = t / (DIM + 1), j = t % (DIM + 1);
+        T v = 0;
+        for (int m = 0; m < NP; ++m) v += (T)pdisc_T(m, j) * sy[mu * NP + m];
+        ob[(long)K1 * Mv + (long)mu * Mp + cell * (DIM + 1) + j] = v;
+      }
     }
     __syncthreads();
   }
@@ -1311,6 +1434,7 @@ CoarseGeom coarse_geom(const st_problem* h) {
   const Level& L = h->lev[0];
   g.dim = h->dim;
   g.K1 = h->K1;
+  g.pdisc = h->P.pressure_space == 1 ? 1 : 0;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = L.n[d];
     g.g2[d] = L.g2[d];
@@ -1339,6 +1463,7 @@ PatchArgs patch_args(const st_problem* h, int level, bool surrogate) {
   for (int d = 0; d < 3; ++d)
     for (int i = 0; i < 9; ++i) pa.M1h[d][i] = h->R.M1[i] * (d < h->dim ? L.h[d] : 1.0);
   pa.surrogate = surrogate ? 1 : 0;
+  pa.pdisc = h->P.pressure_space == 1 ? 1 : 0;
   return pa;
 }
 
@@ -1417,6 +1542,7 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
     const LaunchShape cand[5] = {{nt0, 16L * h->nsm}, {128, 16L * h->nsm}, {256, 8L * h->nsm},
                                  {512, 4L * h->nsm}, {128, 32L * h->nsm}};
     const bool c13 = m->c13 && l == (int)h->lev.size() - 1;
+    const int pdisc = h->P.pressure_space == 1 ? 1 : 0;
     VankaC13 vc;
     memset(&vc, 0, sizeof(vc));
     if (c13) {
@@ -1431,17 +1557,19 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
         if (h->dim == 2)
           vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
                                                                L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1,
-                                                               L.Mv, L.Mp);
+                                                               L.Mv, L.Mp, pdisc);
         else
           vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
                                                                L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1,
-                                                               L.Mv, L.Mp);
+                                                               L.Mv, L.Mp, pdisc);
       } else if (h->dim == 2) {
         vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
-                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp,
+                                                         pdisc);
       } else {
         vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
-                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp,
+                                                         pdisc);
       }
       return cudaGetLastError();
     };
@@ -1471,6 +1599,23 @@ cudaError_t transfer(st_problem* h, MgState* m, int l, bool restrict_, const T* 
   for (int part = 0; part < 2; ++part) {
     const int nblk = part == 0 ? K1 * d : K1;
     const size_t offF = part == 0 ? 0 : (size_t)K1 * F.Mv, offC = part == 0 ? 0 : (size_t)K1 * C.Mv;
+    if (part == 1 && h->P.pressure_space == 1) {
+      // P1disc pressure: cell-wise transfer (into y, or beside the velocity in the last work buffer)
+      cudaError_t e = cudaSuccess;
+      if (restrict_) {
+        const unsigned gr = gridn((size_t)C.ncells * K1, h->nsm);
+        if (d == 2) pdisc_restrict<T, 2><<<gr, 256, 0, h->stream>>>(x + offF, y + offC, C.n[0], C.n[1], 1, K1);
+        else pdisc_restrict<T, 3><<<gr, 256, 0, h->stream>>>(x + offF, y + offC, C.n[0], C.n[1], C.n[2], K1);
+      } else {
+        T* work = ((d - 1) & 1) ? w2 : w1;
+        const unsigned gr = gridn((size_t)F.ncells * K1, h->nsm);
+        if (d == 2) pdisc_prolong<T, 2><<<gr, 256, 0, h->stream>>>(x + offC, work + offF, F.n[0], F.n[1], 1, K1);
+        else pdisc_prolong<T, 3><<<gr, 256, 0, h->stream>>>(x + offC, work + offF, F.n[0], F.n[1], F.n[2], K1);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     int g[3];
     for (int a = 0; a < 3; ++a) g[a] = (int)(restrict_ ? (part == 0 ? F.g2[a] : F.g1[a]) : (part == 0 ? C.g2[a] : C.g1[a]));
     const T* src = x + (restrict_ ? offF : offC);

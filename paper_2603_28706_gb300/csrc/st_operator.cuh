@@ -431,10 +431,19 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
       dst = sX + s * Cfg::SX + r;
     } else {
       const int m = r - NC * NQ;
+      dst = sP + s * NP + m;
+      if (a.pdisc) {
+        // P1disc: the value at vertex m of the cell's affine pressure (pdisc_T)
+        const T* pc = in + (long)K1 * a.Mv + (long)mu * a.Mp + (long)cell * (DIM + 1);
+        T v = pc[0];
+#pragma unroll
+        for (int j = 1; j <= DIM; ++j) v += ((m >> (j - 1)) & 1) ? pc[j] : -pc[j];
+        *dst = v;
+        continue;
+      }
       const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
       const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
       src = in + (long)K1 * a.Mv + (long)mu * a.Mp + g;
-      dst = sP + s * NP + m;
     }
     cp_async_elem<T>(dst, src);
   }
@@ -705,6 +714,17 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
         }
         T* pb = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
                 (long)mu * a.Mp;
+        if (a.pdisc) {
+          // P1disc tests: T^T times the vertex tests, at the cell's own coefficients
+#pragma unroll
+          for (int j = 0; j <= DIM; ++j) {
+            T t = 0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) t += (j == 0 || ((m >> (j - 1)) & 1)) ? pt[m] : -pt[m];
+            pb[(long)cell * (DIM + 1) + j] = t;
+          }
+          continue;
+        }
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
           const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;

@@ -70,6 +70,8 @@ def sizes(p):
     g1 = [p["nx"] + 1, p["ny"] + 1, (p["nz"] + 1) if d == 3 else 1]
     Nq2 = g2[0] * g2[1] * g2[2]
     Nq1 = g1[0] * g1[1] * g1[2]
+    if p.get("pressure_space", 0) == 1:  # P1disc: dim + 1 coefficients per cell
+        Nq1 = p["nx"] * p["ny"] * (p["nz"] if d == 3 else 1) * (d + 1)
     Mv, Mp = d * Nq2, Nq1
     return dict(Nq2=Nq2, Nq1=Nq1, Mv=Mv, Mp=Mp, Nst=(p["k"] + 1) * (Mv + Mp), g2=g2, g1=g1)
 
