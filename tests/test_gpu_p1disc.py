@@ -190,7 +190,7 @@ def mms_problem(n, pressure_space, pp=1.5, dl=0.1, nu=0.1, nui=0.0, t0=0.5, tau=
     p = si.base_params(dim=2, nx=n, ny=n, k=1, t0=t0, dt=tau, p=pp, delta=dl, nu=nu, nu_inf=nui, sigma_max=np.inf,
                        dirichlet_mask=si.ALL_SIDES_2D, q_sign=1.0, pressure_space=pressure_space,
                        levels=max(1, int(np.log2(n))),
-                       coarse_sweeps=8, tol_rel=1e-8, tol_abs=1e-30, newton_maxit=20, fgmres_maxit=400)
+                       coarse_sweeps=8, tol_rel=1e-7, tol_abs=1e-30, newton_maxit=20, fgmres_maxit=400)
     X = si.q2_node_coords(p)
     tt = oracle.time_tables(1)["t"]
     f = np.concatenate([mms_forcing(X[:, 0], X[:, 1], t0 + tau * tm, pp, dl, nu, nui).reshape(-1) for tm in tt])
