@@ -621,6 +621,8 @@ def main():
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--newton-levels", type=int, default=5, help="V-cycle levels of the Newton comparison")
+    ap.add_argument("--newton-cases", default=",".join(c[0] for c in NEWTON_CASES),
+                    help="comma list of the Newton comparison's cases (%s)" % ", ".join(c[0] for c in NEWTON_CASES))
     ap.add_argument("--newton-full", action="store_true",
                     help="with --newton-only: modN, exN and Pic over 5 slabs at the stated (p, delta)")
     ap.add_argument("--config3-only", action="store_true",
@@ -648,7 +650,8 @@ def main():
             res = newton_comparison(st, torch, tuple(args.newton_mesh), arms, cases=NEWTON_CASES[:1],
                                     tangents=("modn", "exn", "pic"), slabs=5, levels=args.newton_levels)
         else:
-            res = newton_comparison(st, torch, tuple(args.newton_mesh), arms, levels=args.newton_levels)
+            cases = tuple(c for c in NEWTON_CASES if c[0] in args.newton_cases.split(","))
+            res = newton_comparison(st, torch, tuple(args.newton_mesh), arms, cases=cases, levels=args.newton_levels)
         print(json.dumps(res))
         return
     if args.config3_only:
