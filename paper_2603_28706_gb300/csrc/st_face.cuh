@@ -26,7 +26,7 @@ struct FaceCfg {
   using D = Dims<DIM>;
   // face slots per batch: small, so that a face CTA fits in the shared memory
   // the volume kernel's CTAs leave free on an SM and the two kernels overlap
-  static constexpr int FS = DIM == 3 ? 16 : 64;
+  static constexpr int FS = DIM == 3 ? 8 : 64;
   // per face slot: PV, PN (NC x NFQ), PT (NC x (DIM-1) x NFQ), FQ (NFQ), FPn (NFP)
   static constexpr int oPV = 0;
   static constexpr int oPN = D::NC * D::NFQ;

@@ -22,7 +22,7 @@ int occupancy_once(K kern, int threads, size_t smem) {
 // all boundary faces of one problem, one launch, writing the face scratch
 // (or, when linearising, the face caches)
 template <int DIM, int K1, typename T, int MODE, int TAN>
-cudaError_t launch_faces_t(const st_problem* h, const Level& L, const OpArgs& a, cudaStream_t st) {
+cudaError_t launch_faces_t(const st_problem* h, const Level& L, const OpArgs& a, cudaStream_t st, long fcap = 0) {
   using FCfg = FaceCfg<DIM, T>;
   auto fkern = st_face_kernel<DIM, K1, T, MODE, TAN>;
   static const int focc = occupancy_once(fkern, OP_THREADS, FCfg::smem_bytes);
@@ -30,7 +30,7 @@ cudaError_t launch_faces_t(const st_problem* h, const Level& L, const OpArgs& a,
   const long nslots = L.nfaces * K1;
   if (nslots == 0) return cudaSuccess;
   long fgrid = (nslots + FCfg::FS - 1) / FCfg::FS;
-  const long fcap = 8L * h->nsm;
+  if (fcap <= 0) fcap = 8L * h->nsm;
   if (fgrid > fcap) fgrid = fcap;
   fkern<<<(unsigned)fgrid, OP_THREADS, FCfg::smem_bytes, st>>>(a, L.d_face_cell, L.d_face_side, nslots,
                                                                 reinterpret_cast<T*>(h->d_fscr));
@@ -116,58 +116,67 @@ cudaError_t launch_op_t(const st_problem* h, const Level& L, OpArgs& a) {
   if (occ == 0) return cudaErrorInvalidConfiguration;
   // The volume kernel (one launch over all cells in colour order) writes
   // every cell's contributions into the private buffer of its colour class
-  // with plain stores.  The face kernel (all boundary faces, one launch) is
-  // enqueued after it on an internal stream that depends only on the work
-  // before the volume kernel, so its small CTAs fill the shared memory and
-  // registers the volume kernel's CTAs leave free on every SM and run beside
-  // them; it writes only the face scratch (or, when linearising, the face
+  // with plain stores.  The face kernel (all boundary faces, one launch) runs
+  // on an internal stream that depends only on the work before the volume
+  // kernel; its small CTAs fit into the shared memory and registers the
+  // volume kernel's CTAs leave free on every SM, so the two can run side by
+  // side.  It writes only the face scratch (or, when linearising, the face
   // cache).  The caller's stream then waits for the face kernel;
   // st_cbuf_sum and st_face_add form out = sum of the class buffers + face
-  // contributions, one thread per node.
-  cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
-  if (e != cudaSuccess) return e;
+  // contributions.
   set_volume_args<T>(h, L, a);
-  {
-    // Default: every resident CTA slot gets an equal share of the cells when
-    // there are at least half a batch per slot; smaller meshes use full
-    // batches.  The Jacobian action (the hot call) autotunes the number of
-    // cells per CTA: the balanced share of one, two or four CTA waves, or one
-    // batch of C cells per CTA (each CTA always runs batches of C cells).
-    const long cap = (long)occ * h->nsm;
-    const long full = (L.ncells + Cfg::C - 1) / Cfg::C;
-    long grid = full;
-    if (L.ncells >= cap * (Cfg::C / 2)) grid = cap;
-    if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    if (MODE == OP_JAC) {
-      long cand[4] = {grid, 2 * cap, 4 * cap, full};
-      for (long& c : cand) c = c < 1 ? 1 : (c > full ? full : c);
-      const std::string key = "st_op_kernel<" + std::to_string(DIM) + "," + std::to_string(K1) + "," +
-                              (sizeof(T) == 8 ? "double" : "float") + ",OP_JAC," + std::to_string(TAN) +
-                              "> cells=" + std::to_string(L.ncells);
-      const int pick = tune_pick(
-          key, 4,
-          [&](int i) {
-            kern<<<(unsigned)cand[i], Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
-            return cudaGetLastError();
-          },
-          [&](int i) { return "cells/CTA=" + std::to_string((L.ncells + cand[i] - 1) / cand[i]); }, h->stream);
-      grid = cand[pick];
-    }
-    kern<<<(unsigned)grid, Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  const std::string tag = std::to_string(DIM) + "," + std::to_string(K1) + "," +
+                          (sizeof(T) == 8 ? "double" : "float") + ",OP_JAC," + std::to_string(TAN) +
+                          "> cells=" + std::to_string(L.ncells);
+  // Default: every resident CTA slot gets an equal share of the cells when
+  // there are at least half a batch per slot; smaller meshes use full
+  // batches.  The Jacobian action (the hot call) autotunes the number of
+  // cells per CTA: the balanced share of one, two or four CTA waves, or one
+  // batch of C cells per CTA (each CTA always runs batches of C cells).
+  const long cap = (long)occ * h->nsm;
+  const long full = (L.ncells + Cfg::C - 1) / Cfg::C;
+  long grid = full;
+  if (L.ncells >= cap * (Cfg::C / 2)) grid = cap;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  if (MODE == OP_JAC) {
+    long cand[4] = {grid, 2 * cap, 4 * cap, full};
+    for (long& c : cand) c = c < 1 ? 1 : (c > full ? full : c);
+    const int pick = tune_pick(
+        "st_op_kernel<" + tag, 4,
+        [&](int i) {
+          kern<<<(unsigned)cand[i], Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
+          return cudaGetLastError();
+        },
+        [&](int i) { return "cells/CTA=" + std::to_string((L.ncells + cand[i] - 1) / cand[i]); }, h->stream);
+    grid = cand[pick];
   }
-  e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
-  if (e == cudaSuccess) e = launch_faces_t<DIM, K1, T, MODE, TAN>(h, L, a, h->s_face);
-  if (e != cudaSuccess) return e;
-  e = launch_cip_t<DIM, K1, T, MODE>(h, L, a, h->stream);
-  if (e != cudaSuccess) return e;
-  e = cudaEventRecord(h->ev_join, h->s_face);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
-  if (e != cudaSuccess) return e;
-  if (MODE != OP_LIN) e = launch_node_sum_t<DIM, K1, T>(h, L, a, h->stream);
-  return e;
+  // The whole sequence: the volume kernel, then the face kernel in the space
+  // it leaves.  Tuned over the whole apply: the volume grid chosen alone, or
+  // the balanced one-wave grid, whose CTAs all start at once and so leave
+  // the scheduler free to place face CTAs beside them.
+  auto sequence = [&](long vgrid) -> cudaError_t {
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)vgrid, Cfg::NT, Cfg::smem_bytes, h->stream>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_face, h->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_faces_t<DIM, K1, T, MODE, TAN>(h, L, a, h->s_face);
+    if (e == cudaSuccess) e = launch_cip_t<DIM, K1, T, MODE>(h, L, a, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->s_face);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    if (e == cudaSuccess && MODE != OP_LIN) e = launch_node_sum_t<DIM, K1, T>(h, L, a, h->stream);
+    return e;
+  };
+  if (MODE == OP_JAC) {
+    const long vg[2] = {grid, cap < full ? cap : full};
+    const int pick = tune_pick(
+        "jacobian apply<" + tag, vg[0] == vg[1] ? 1 : 2, [&](int i) { return sequence(vg[i]); },
+        [&](int i) { return "volume cells/CTA=" + std::to_string((L.ncells + vg[i] - 1) / vg[i]) + ", faces beside"; },
+        h->stream);
+    grid = vg[pick];
+  }
+  return sequence(grid);
 }
 
 // Several problems (same dim and k) in one persistent volume launch over the
