@@ -818,18 +818,64 @@ inline bool try_gj_reg(R* F, int* piv, int N, long count, int* err, int nsm, cud
 
 // The register Gauss-Jordan inversion (implicit pivoting, see
 // gj_invert_reg_kernel) for complex matrices stored as interleaved (re, im)
-// pairs, column-major; R = float or double; pivot: largest |a_ik|^2.
+// pairs, column-major; R = float or double; pivot: largest |a_ik|^2 (lowest
+// row on ties).  Two barriers per elimination step: the warp that owns
+// column k+1 updates it first and then searches the next pivot while the
+// other warps finish their updates; pivot column, pivot row and pivot index
+// are double-buffered by step parity.
 template <int RPL, int CPW, int NW, typename R>
-__global__ void __launch_bounds__(32 * NW) gj_invert_reg_cplx(R* __restrict__ F, int N, long count,
-                                                              int* __restrict__ err) {
+__device__ __forceinline__ void gj_cplx_search(const R (&ar)[RPL][CPW], const R (&ai)[RPL][CPW], int c_own, int N,
+                                               int lane, int k, int* s_used, int* s_kinv, int* s_pv, R* s_col,
+                                               int* s_pb, int* err) {
+  R best = (R)-1;
+  int bi = 0x7fffffff;
+#pragma unroll
+  for (int c = 0; c < CPW; ++c)
+    if (c == c_own) {
+#pragma unroll
+      for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        s_col[2 * i] = ar[r][c];
+        s_col[2 * i + 1] = ai[r][c];
+        if (i < N && !s_used[i]) {
+          if (bi == 0x7fffffff) bi = i;
+          const R v = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
+      }
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    *s_pb = bi;
+    s_used[bi] = 1;
+    s_kinv[bi] = k;
+    s_pv[k] = bi;
+    if (!(best > (R)0)) atomicExch(err, 1);
+  }
+}
+
+template <int RPL, int CPW, int NW, typename R, int MINB = 1>
+__global__ void __launch_bounds__(32 * NW, MINB) gj_invert_reg_cplx(R* __restrict__ F, int N, long count,
+                                                                    int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char gc_raw[];
   R* S = reinterpret_cast<R*>(gc_raw);                          // 2 N^2 staging of the result
-  R* s_col = S + 2 * (size_t)N * N;                              // column k (2 x 32 RPL)
-  R* s_row = s_col + 2 * 32 * RPL;                               // pivot row (2 x NW CPW)
-  int* s_used = reinterpret_cast<int*>(s_row + 2 * NW * CPW);
+  R* s_col = S + 2 * (size_t)N * N;                              // column k, two buffers of 2 x 32 RPL
+  R* s_row = s_col + 4 * 32 * RPL;                               // pivot row, two buffers of 2 x NW CPW
+  int* s_used = reinterpret_cast<int*>(s_row + 4 * NW * CPW);
   int* s_kinv = s_used + 32 * RPL;
   int* s_pv = s_kinv + 32 * RPL;
-  __shared__ int s_p;
+  __shared__ int s_p[2];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long m = blockIdx.x; m < count; m += gridDim.x) {
     const R* G = F + m * 2 * (long)N * N;
@@ -847,67 +893,32 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_cplx(R* __restrict__ F,
     }
     for (int i = threadIdx.x; i < 32 * RPL; i += blockDim.x) s_used[i] = (i < N) ? 0 : 1;
     __syncthreads();
+    if (w == 0) gj_cplx_search<RPL, CPW, NW, R>(ar, ai, 0, N, lane, 0, s_used, s_kinv, s_pv, s_col, &s_p[0], err);
+    __syncthreads();
     for (int k = 0; k < N; ++k) {
-      const int wk = k % NW, ck = k / NW;
-      if (w == wk) {
-        R best = (R)-1;
-        int bi = 0x7fffffff;
-#pragma unroll
-        for (int c = 0; c < CPW; ++c)
-          if (c == ck) {
-#pragma unroll
-            for (int r = 0; r < RPL; ++r) {
-              const int i = lane + 32 * r;
-              s_col[2 * i] = ar[r][c];
-              s_col[2 * i + 1] = ai[r][c];
-              if (i < N && !s_used[i]) {
-                if (bi == 0x7fffffff) bi = i;
-                const R v = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
-                if (v > best) {
-                  best = v;
-                  bi = i;
-                }
-              }
-            }
-          }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const R ov = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > best || (ov == best && oi < bi)) {
-            best = ov;
-            bi = oi;
-          }
-        }
-        if (lane == 0) {
-          s_p = bi;
-          s_used[bi] = 1;
-          s_kinv[bi] = k;
-          s_pv[k] = bi;
-          if (!(best > (R)0)) atomicExch(err, 1);
-        }
-      }
-      __syncthreads();
-      const int p = s_p, lp = p & 31, rp = p >> 5;
+      const int b = k & 1, wk = k % NW, ck = k / NW;
+      R* colb = s_col + b * 2 * 32 * RPL;
+      R* rowb = s_row + b * 2 * NW * CPW;
+      const int p = s_p[b], lp = p & 31, rp = p >> 5;
       if (lane == lp) {
 #pragma unroll
         for (int r = 0; r < RPL; ++r)
           if (r == rp) {
 #pragma unroll
             for (int c = 0; c < CPW; ++c) {
-              s_row[2 * (w + NW * c)] = ar[r][c];
-              s_row[2 * (w + NW * c) + 1] = ai[r][c];
+              rowb[2 * (w + NW * c)] = ar[r][c];
+              rowb[2 * (w + NW * c) + 1] = ai[r][c];
             }
           }
       }
       __syncthreads();
-      const R dr = s_row[2 * k], di = s_row[2 * k + 1], dn = dr * dr + di * di;
+      const R dr = rowb[2 * k], di = rowb[2 * k + 1], dn = dr * dr + di * di;
       const R ir = dr / dn, ii = -di / dn;  // 1 / d
       R fr[RPL], fi[RPL];
 #pragma unroll
       for (int r = 0; r < RPL; ++r) {
-        fr[r] = s_col[2 * (lane + 32 * r)];
-        fi[r] = s_col[2 * (lane + 32 * r) + 1];
+        fr[r] = colb[2 * (lane + 32 * r)];
+        fi[r] = colb[2 * (lane + 32 * r) + 1];
       }
       if (lane == lp) {
 #pragma unroll
@@ -931,7 +942,7 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_cplx(R* __restrict__ F,
 #pragma unroll
       for (int c = 0; c < CPW; ++c) {
         const int j = w + NW * c;
-        R xr = s_row[2 * j], xi = s_row[2 * j + 1];
+        R xr = rowb[2 * j], xi = rowb[2 * j + 1];
         if (j == k) {
           xr = 1;
           xi = 0;
@@ -951,6 +962,10 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_cplx(R* __restrict__ F,
             }
         }
       }
+      // the owner of column k+1 searches the next pivot on its updated column
+      if (k + 1 < N && w == (k + 1) % NW)
+        gj_cplx_search<RPL, CPW, NW, R>(ar, ai, (k + 1) / NW, N, lane, k + 1, s_used, s_kinv, s_pv,
+                                        s_col + (b ^ 1) * 2 * 32 * RPL, &s_p[b ^ 1], err);
       __syncthreads();
     }
 #pragma unroll
@@ -975,28 +990,32 @@ __global__ void __launch_bounds__(32 * NW) gj_invert_reg_cplx(R* __restrict__ F,
   }
 }
 
-template <int RPL, int CPW, typename R>
+template <int RPL, int CPW, int NW, int MINB, typename R>
 cudaError_t launch_gj_cplx(R* F, int N, long count, int* err, int nsm, cudaStream_t st) {
-  constexpr int NW = 16;
-  const size_t sm = 2 * (size_t)N * N * sizeof(R) + 2 * (32 * RPL + NW * CPW) * sizeof(R) + 3 * 32 * RPL * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(gj_invert_reg_cplx<RPL, CPW, NW, R>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = gj_invert_reg_cplx<RPL, CPW, NW, R, MINB>;
+  const size_t sm = 2 * (size_t)N * N * sizeof(R) + 4 * (32 * RPL + NW * CPW) * sizeof(R) + 3 * 32 * RPL * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int occ = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gj_invert_reg_cplx<RPL, CPW, NW, R>, 32 * NW, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * NW, sm);
   if (e != cudaSuccess) return e;
   const long cap = (long)(occ > 0 ? occ : 1) * nsm;
   const unsigned g = (unsigned)(count < cap ? count : cap);
-  gj_invert_reg_cplx<RPL, CPW, NW, R><<<g, 32 * NW, sm, st>>>(F, N, count, err);
+  kern<<<g, 32 * NW, sm, st>>>(F, N, count, err);
   return cudaGetLastError();
 }
 
-// complex patches of the time-diagonalised surrogate (N = NE: 22 in 2D, 89 in 3D)
+// complex patches of the time-diagonalised surrogate (N = NE: 22 in 2D, 89 in
+// 3D).  3D FP32: 8 warps per matrix with the registers capped for two CTAs per
+// SM (122 registers, no spills), so that one CTA's pivot search and barriers
+// overlap the other's updates; FP64 keeps 16 warps per matrix (its 8-warp
+// form would spill).
 template <typename R>
 cudaError_t invert_patches_cplx(R* F, int N, long count, int* err, int nsm, cudaStream_t st) {
-  if (N <= 32) return launch_gj_cplx<1, 2, R>(F, N, count, err, nsm, st);
-  if (N <= 96) return launch_gj_cplx<3, 6, R>(F, N, count, err, nsm, st);
-  return cudaErrorInvalidValue;
+  if (N <= 32) return launch_gj_cplx<1, 2, 16, 1, R>(F, N, count, err, nsm, st);
+  if (N > 96) return cudaErrorInvalidValue;
+  if constexpr (sizeof(R) == 4) return launch_gj_cplx<3, 12, 8, 2, R>(F, N, count, err, nsm, st);
+  else return launch_gj_cplx<3, 6, 16, 1, R>(F, N, count, err, nsm, st);
 }
 
 // Time-diagonalised surrogate patch solve (see TimeEig), all patches in one
