@@ -1172,10 +1172,13 @@ __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __re
 // (A_l x)|_K for all cells in one launch, into the buffer of the cell's
 // colour class: per cell and node mu the element matrix E[cell][mu] (spatial
 // part, times tau w_mu) and the temporal mass coupling sum_nu K_t[mu][nu]
-// M_e x_nu on the velocity; colour_sum forms A_l x.
+// M_e x_nu on the velocity; colour_sum forms A_l x.  split = 0: one work item
+// per cell; split = 1: one per (cell, mu), each computing that node's rows
+// (more parallel work on the small coarse levels).
 template <int DIM, typename T>
 __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, const T* __restrict__ x, T* __restrict__ cb,
-                             long cstride, ColourMap cm, long ncells, long Nq2, long Nq1, long Mv, long Mp) {
+                             long cstride, ColourMap cm, long ncells, long Nq2, long Nq1, long Mv, long Mp,
+                             int split) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   __shared__ T sx[MAXN];
   __shared__ long sg[MAXN];
@@ -1193,7 +1196,10 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
     for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
     smass[t] = (T)m;
   }
-  for (long li = blockIdx.x; li < ncells; li += gridDim.x) {
+  const int P = split ? K1 : 1;
+  for (long it = blockIdx.x; it < ncells * P; it += gridDim.x) {
+    const long li = it / P;
+    const int mlo = split ? (int)(it % P) : 0, mhi = split ? mlo + 1 : K1;  // nodes whose rows this item computes
     int col, ex, ey, ez;
     colour_cell(cm, li, col, ex, ey, ez);
     const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
@@ -1221,8 +1227,8 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
       sx[r] = x[g];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < K1 * NC * NQ; t += blockDim.x) {
-      const int mu = t / (NC * NQ), v = t % (NC * NQ);
+    for (int t = threadIdx.x; t < (mhi - mlo) * NC * NQ; t += blockDim.x) {
+      const int mu = mlo + t / (NC * NQ), v = t % (NC * NQ);
       T acc = 0;
       for (int nu = 0; nu < K1; ++nu) acc += (T)pa.Kt[mu * K1 + nu] * sx[nu * NE + v];
       skt[mu][v] = acc;
@@ -1232,13 +1238,15 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
     // temporal mass coupling; the loop runs over whole warps so that every
     // lane takes part in the half-warp shuffles
     const int hl = lane & 15, half = lane >> 4;
-    for (int r0 = 2 * warp; r0 < N; r0 += 2 * nwarp) {
+    const int rlo = mlo * NE, rhi = mhi * NE;
+    for (int r0 = rlo + 2 * warp; r0 < rhi; r0 += 2 * nwarp) {
       const int r = r0 + half;
-      const bool act = r < N;
+      const bool act = r < rhi;
       const int mu = act ? r / NE : 0, i = act ? r % NE : 0;
       const T* Er = E + (cell * K1 + mu) * NE * NE + (long)i * NE;
       T acc = 0;
       if (act) {
+#pragma unroll
         for (int j = hl; j < NE; j += 16) acc = fma(Er[j], sx[mu * NE + j], acc);
         if (i < NC * NQ) {
           const int c = i / NQ, a = i % NQ;
@@ -1254,8 +1262,8 @@ __global__ void coarse_apply(const T* __restrict__ E, int K1, PatchArgs pa, cons
     }
     if (pa.pdisc) {
       __syncthreads();
-      for (int t = threadIdx.x; t < K1 * (DIM + 1); t += blockDim.x) {
-        const int mu = t / (DIM + 1), j = t % (DIM + 1);
+      for (int t = threadIdx.x; t < (mhi - mlo) * (DIM + 1); t += blockDim.x) {
+        const int mu = mlo + t / (DIM + 1), j = t % (DIM + 1);
         T v = 0;
         for (int m = 0; m < NP; ++m) v += (T)pdisc_T(m, j) * sy[mu * NP + m];
         ob[(long)K1 * Mv + (long)mu * Mp + cell * (DIM + 1) + j] = v;
@@ -1520,22 +1528,28 @@ cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
   PatchArgs pa = patch_args(h, l, false);
   const ColourMap cm = colour_map(h, L);
   T* cb = (T*)m->L[l].cbuf;
-  // autotuned launch shape (threads per CTA, CTAs per SM); one CTA per cell at a time
-  const LaunchShape cand[4] = {{128, 8L * h->nsm}, {256, 8L * h->nsm}, {128, 16L * h->nsm}, {256, 4L * h->nsm}};
+  // autotuned launch shape (threads per CTA, CTAs per SM, one work item per
+  // cell or per (cell, node))
+  const LaunchShape cand[7] = {{128, 8L * h->nsm},  {256, 8L * h->nsm},  {128, 16L * h->nsm}, {256, 4L * h->nsm},
+                               {128, 16L * h->nsm}, {256, 8L * h->nsm},  {512, 4L * h->nsm}};
+  const int csplit[7] = {0, 0, 0, 0, 1, 1, 1};
   auto run = [&](int i) {
-    const unsigned g = (unsigned)(L.ncells < cand[i].grid ? L.ncells : cand[i].grid);
+    const long items = L.ncells * (csplit[i] ? h->K1 : 1);
+    const unsigned g = (unsigned)(items < cand[i].grid ? items : cand[i].grid);
     if (h->dim == 2)
       coarse_apply<2, T><<<g, cand[i].threads, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm,
-                                                               L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+                                                               L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp, csplit[i]);
     else
       coarse_apply<3, T><<<g, cand[i].threads, 0, h->stream>>>((const T*)m->L[l].E, h->K1, pa, x, cb, L.Nst, cm,
-                                                               L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp);
+                                                               L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp, csplit[i]);
     return cudaGetLastError();
   };
   const int pick = tune_pick(
       "coarse_apply<" + std::to_string(h->dim) + "," + (sizeof(T) == 8 ? "double" : "float") + "> K1=" +
           std::to_string(h->K1) + " cells=" + std::to_string(L.ncells),
-      4, run, [&](int i) { return shape_label(cand[i], h->nsm); }, h->stream);
+      h->K1 > 1 ? 7 : 4, run,
+      [&](int i) { return shape_label(cand[i], h->nsm) + (csplit[i] ? " per (cell, node)" : " per cell"); },
+      h->stream);
   cudaError_t e = run(pick);
   if (e != cudaSuccess) return e;
   colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, y, L.Nst, (T)1, 0);
