@@ -17,6 +17,12 @@ restatement on the oracle's assembled matrices, small meshes only:
                      I (x) J^rep, temporal matrices unchanged)
   vanka_step         d <- d + omega sum_K R_K^T A_K^{-1} R_K (r - A d)
                      (eq. stmg-vanka-update), one defect per step
+                     (smoother="additive"); or, smoother="colour", the same
+                     update taken class by class over the 2^d colour classes
+                     of cells (cell parities (px, py, pz), class px + 2 py +
+                     4 pz, in that order), a fresh defect before each class:
+                     multiplicative Schwarz between classes, additive within
+                     one (cells of a class share no dof)
   vcycle             pre-smoothing, restriction, recursion, coarsest-level
                      treatment, prolongation, post-smoothing
 Readings (the paper defers to its references here): the coarsest level is
@@ -148,6 +154,30 @@ def surrogate_operator(p, var, U):
     return assemble_csr(p, var, rep_state(p, U))
 
 
+def colour_classes(p):
+    """Cells of each colour class, class px + 2 py + 4 pz holding the cells
+    whose coordinates (x fastest in the linear cell index) have parities
+    (px, py, pz); two cells of one class are at least one cell apart."""
+    d = p["dim"]
+    nx, ny, nz = p["nx"], p["ny"], (p["nz"] if d == 3 else 1)
+    c = np.arange(nx * ny * nz)
+    cls = (c % nx) % 2 + 2 * (((c // nx) % ny) % 2) + 4 * ((c // (nx * ny)) % 2)
+    return [np.where(cls == k)[0] for k in range(2 ** d)]
+
+
+def colour_sweep(A, Ainv, dofs, classes, omega, r, d):
+    """One multiplicative Vanka step over the classes in order: for each class
+    a fresh defect r - A d, then d += omega sum_{K in class} R_K^T A_K^{-1} R_K
+    defect."""
+    for cells in classes:
+        defect = r - A @ d
+        corr = np.zeros_like(d)
+        for c in cells:
+            corr[dofs[c]] += Ainv[c] @ defect[dofs[c]]
+        d = d + omega * corr
+    return d
+
+
 class Hierarchy:
     """Levels 0 (coarsest) .. L (finest) with operators and patch inverses.
 
@@ -157,10 +187,13 @@ class Hierarchy:
     (the refresh rule of Sec. 6.3 keeps them otherwise)."""
 
     def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True,
-                 coarse_solve="sweeps"):
+                 coarse_solve="sweeps", smoother="additive"):
         if coarse_solve not in ("sweeps", "direct"):
             raise ValueError("coarse_solve must be 'sweeps' or 'direct'")
+        if smoother not in ("additive", "colour"):
+            raise ValueError("smoother must be 'additive' or 'colour'")
         self.p, self.levels = p, levels
+        self.smoother = smoother
         self.coarse_solve = coarse_solve
         self.lu0 = None
         self.omega = omega
@@ -199,6 +232,8 @@ class Hierarchy:
 
     def vanka_step(self, l, r, d):
         A = self.op(l)
+        if self.smoother == "colour":
+            return colour_sweep(A, self.Ainv[l], self.dofs[l], colour_classes(self.params[l]), self.omega, r, d)
         defect = r - A @ d
         corr = np.zeros_like(d)
         for c, dof in enumerate(self.dofs[l]):
