@@ -184,16 +184,23 @@ CONFIG3_WORKLOAD = ("3D unit cube 64^3 hexes, Q2/Q1, dG(2) 3 Radau points, dt=0.
                     "by 8 Vanka sweeps")
 
 
-def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300):
+def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300, smoother=0, omega=None, arms=("mixed", "fp64"),
+                  dt=None):
     """The 64^3, dG(2) linear solve with the FP32 V-cycle (mixed) and the FP64
     V-cycle: seconds of the preconditioner set-up and of the FGMRES solve,
     iterations and final relative residual per arm."""
-    p = si.config(3, nx=mesh, ny=mesh, nz=mesh, levels=levels, coarse_solve=coarse)
+    p = si.config(3, nx=mesh, ny=mesh, nz=mesh, levels=levels, coarse_solve=coarse, smoother=smoother)
+    if omega is not None:
+        p["omega"] = omega
+    if dt is not None:
+        p["dt"] = dt
     s = si.sizes(p)
     K1 = p["k"] + 1
     res = {"workload": CONFIG3_WORKLOAD.replace("64^3", "%d^3" % mesh), "levels": levels,
-           "coarse_solve": coarse, "dofs": s["Nst"]}
+           "coarse_solve": coarse, "smoother": smoother, "omega": p["omega"], "dt": p["dt"], "dofs": s["Nst"]}
     for arm, prec in (("mixed", st.ST_FP32), ("fp64", st.ST_FP64)):
+        if arm not in arms:
+            continue
         U = torch.from_numpy(si.fourier_state(p, 0)).cuda()
         vprev = U[(K1 - 1) * s["Mv"]:K1 * s["Mv"]].clone() + 0.1 * torch.from_numpy(si.uniform(s["Mv"], 2)).cuda()
         prob = st.Problem(p)
@@ -367,7 +374,10 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
     for _ in range(slabs):
         status, info = prob.newton_step(tangent, U, vprev, vcycle_prec=vprec, raise_on_fail=False)
         if status != st.ST_OK:
-            fail = {"slab": len(n_nl), "newton_iters": info["newton_iters"], "fgmres_iters": info["fgmres_iters_total"],
+            kind = ("linesearch" if status == st.ST_LINESEARCH_FAILED else
+                    "newton_cap" if info["newton_iters"] >= p["newton_maxit"] else "linear")
+            fail = {"slab": len(n_nl), "kind": kind, "newton_iters": info["newton_iters"],
+                    "fgmres_iters": info["fgmres_iters_total"],
                     "res_ratio": info["res_norm_final"] / max(info["res_norm_initial"], 1e-300)}
             break
         n_nl.append(info["newton_iters"])
@@ -379,7 +389,7 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
             "W": work(n_l, n) if ok else None, "n_nl_mean": float(np.mean(n_nl)) if ok else None}
 
 
-def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=None):
+def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=None, smoother="additive"):
     """Analogue of the solver evaluation of Sec. 7 (Table newton-compact, eq.
     work, eq. perf-profile) on synthetic channel problems: every (p, delta,
     mesh) instance with Pic, exN and modN."""
@@ -394,7 +404,8 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=No
                 prm = si.base_params(dim=2, nx=4 * n, ny=n, Lx=4.0, Ly=1.0, k=1, dt=1.0, p=pe, delta=delta,
                                      nu=1e-3, nu_inf=0.0, sigma_max=1e-4, inflow_profile=1, vbar=0.1,
                                      levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30,
-                                     finest_patches=0 if patches == "surrogate" else 1)
+                                     finest_patches=0 if patches == "surrogate" else 1,
+                                     smoother=0 if smoother == "additive" else 1)
                 if omega is not None:
                     prm["omega"] = omega
                 row = {"cells": 4 * n * n, "p": pe, "delta": delta}
@@ -404,7 +415,7 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=No
                 W.append([row[v]["W"] if row[v]["ok"] else np.inf for v in SWEEP_VARIANTS])
     taus = [1.0, 1.25, 1.5, 2.0, 3.0, 5.0, 10.0]
     prof = perf_profile(W, taus)
-    return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "finest_patches": patches,
+    return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "finest_patches": patches, "smoother": smoother,
             "omega": omega if omega is not None else si.base_params(dim=2)["omega"],
             "meshes_cells": [4 * n * n for n in SWEEP_MESHES],
             "p": list(SWEEP_P),
@@ -618,6 +629,8 @@ def main():
     ap.add_argument("--sweep-patches", default="surrogate", choices=["surrogate", "exact"],
                     help="finest-level Vanka patches of the sweep: the surrogate of eq. surrogate-diag or exact")
     ap.add_argument("--sweep-omega", type=float, default=None, help="Vanka damping of the sweep (default: 2D default)")
+    ap.add_argument("--sweep-smoother", default="additive", choices=["additive", "colour"],
+                    help="Vanka step of the sweep: additive (eq. stmg-vanka-update) or colour-multiplicative")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--newton-levels", type=int, default=5, help="V-cycle levels of the Newton comparison")
@@ -630,6 +643,11 @@ def main():
     ap.add_argument("--config3-mesh", type=int, default=64)
     ap.add_argument("--config3-levels", type=int, default=4)
     ap.add_argument("--config3-coarse", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--config3-smoother", type=int, default=0, choices=[0, 1],
+                    help="Vanka step: 0 additive, 1 colour-multiplicative")
+    ap.add_argument("--config3-omega", type=float, default=None)
+    ap.add_argument("--config3-dt", type=float, default=None)
+    ap.add_argument("--config3-arms", default="mixed,fp64")
     args = ap.parse_args()
 
     p, U, dU, vp = si.workload(2)
@@ -655,7 +673,9 @@ def main():
         print(json.dumps(res))
         return
     if args.config3_only:
-        print(json.dumps(config3_solve(st, torch, args.config3_mesh, args.config3_levels, args.config3_coarse)))
+        print(json.dumps(config3_solve(st, torch, args.config3_mesh, args.config3_levels, args.config3_coarse,
+                                       smoother=args.config3_smoother, omega=args.config3_omega,
+                                       arms=tuple(args.config3_arms.split(",")), dt=args.config3_dt)))
         return
     if args.batched_only:
         res = batched_comparison(st, torch)
@@ -663,7 +683,8 @@ def main():
         print(json.dumps(res))
         return
     if args.sweep:
-        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches, args.sweep_omega)))
+        print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches, args.sweep_omega,
+                                          args.sweep_smoother)))
         return
     stream = torch.cuda.current_stream()
     if args.cip_only:

@@ -107,6 +107,13 @@ typedef struct {
                                  cell the basis 1, 2 r_a - 1 (r_a the cell's
                                  reference coordinates), P_mu = [cell][1 + dim]
                                  with cells lexicographic, x fastest                */
+  int smoother;               /* 0: additive Vanka step of eq. stmg-vanka-update (one
+                                 defect per step); 1: the same update taken class by
+                                 class over the 2^dim colour classes of cells (cell
+                                 parities px + 2 py + 4 pz, in that order), a fresh
+                                 defect before each class: multiplicative between
+                                 classes, additive inside one (its cells share no
+                                 dof); 2^dim defects per step                        */
 } st_params;
 
 typedef struct {
@@ -184,8 +191,9 @@ st_status st_mnorm(st_problem* h, const void* r, double* out);
  * st_vanka_smooth / st_vcycle when missing. */
 st_status st_precond_setup(st_problem* h, st_prec prec);
 
-/* `sweeps` additive Vanka steps on level `level` (eq. stmg-vanka-update):
- *   d <- d + omega sum_K R_K^T A_K^{-1} R_K (r - A_l d),
+/* `sweeps` Vanka steps on level `level` (eq. stmg-vanka-update):
+ *   d <- d + omega sum_K R_K^T A_K^{-1} R_K (r - A_l d)
+ * (smoother = 1: over one colour class at a time, a fresh defect each),
  * cell patches K with all k+1 time nodes; A_K exact on coarse levels and the
  * surrogate of eq. surrogate-diag on the finest level (exact there too with
  * finest_patches = 1).  r, d: slab vectors of

@@ -1029,14 +1029,15 @@ struct VankaC13 {
 template <int DIM, typename T>
 __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int K1, const T* __restrict__ defect,
                                       T* __restrict__ cb, long cstride, int n0, int n1, int n2, ColourMap cm,
-                                      long ncells, long Nq2, long Nq1, long Mv, long Mp, int pdisc) {
+                                      long li0, long nli, long Nq2, long Nq1, long Mv, long Mp, int pdisc,
+                                      T* __restrict__ dd, T omega) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE, nb = vc.nb;
   __shared__ T sx[MAXN];
   __shared__ long sg[MAXN];
   __shared__ T ss[MAX_K1][NE][2], sz[MAX_K1][NE][2];
   const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
-  for (long li = blockIdx.x; li < ncells; li += gridDim.x) {
+  for (long li = li0 + blockIdx.x; li < li0 + nli; li += gridDim.x) {
     int col, ex, ey, ez;
     colour_cell(cm, li, col, ex, ey, ez);
     const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
@@ -1103,7 +1104,10 @@ __global__ void vanka_patch_solve_c13(const T* __restrict__ G, VankaC13 vc, int 
       const int mu = r / NE, p = r % NE;
       T x = 0;
       for (int b = 0; b < nb; ++b) x += (T)vc.tout[b][mu][0] * sz[b][p][0] - (T)vc.tout[b][mu][1] * sz[b][p][1];
-      if (sg[r] >= 0) ob[sg[r]] = x;
+      if (sg[r] >= 0) {
+        if (dd) dd[sg[r]] += omega * x;
+        else ob[sg[r]] = x;
+      }
     }
     __syncthreads();
   }
@@ -1121,20 +1125,22 @@ cudaError_t invert_patches(T* F, int* piv, int N, long count, int* err, int nsm,
 }
 
 // ------------------------------------------------------------ Vanka solve
-// All patches (cells) in one launch: x = A_K^{-1} defect|_K with the explicit
-// inverse (a matrix-vector product streamed column by column), stored into
-// the buffer of the cell's colour class (cells of one class share no dof);
-// the caller adds omega times the class buffers into d.
+// The patches of colour-ordered cells li0 .. li0 + nli - 1 in one launch:
+// x = A_K^{-1} defect|_K with the explicit inverse (a matrix-vector product
+// streamed column by column), stored into the buffer of the cell's colour
+// class (cells of one class share no dof; the caller adds omega times the
+// class buffers into d), or, with dd set (the cells of one class), added as
+// omega x into dd directly.
 template <int DIM, typename T>
 __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __restrict__ defect, T* __restrict__ cb,
-                                  long cstride, int n0, int n1, int n2, ColourMap cm, long ncells, long Nq2, long Nq1,
-                                  long Mv, long Mp, int pdisc) {
+                                  long cstride, int n0, int n1, int n2, ColourMap cm, long li0, long nli, long Nq2,
+                                  long Nq1, long Mv, long Mp, int pdisc, T* __restrict__ dd, T omega) {
   constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NP = DIM == 3 ? 8 : 4, NE = NC * NQ + NP;
   const int N = K1 * NE;
   __shared__ T sx[MAXN];
   __shared__ long sg[MAXN];
   const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
-  for (long li = blockIdx.x; li < ncells; li += gridDim.x) {
+  for (long li = li0 + blockIdx.x; li < li0 + nli; li += gridDim.x) {
     int col, ex, ey, ez;
     colour_cell(cm, li, col, ex, ey, ez);
     const long cell = ex + (long)n0 * (ey + (long)n1 * ez);
@@ -1162,7 +1168,10 @@ __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __re
       T acc = 0;
 #pragma unroll 8
       for (int j = 0; j < N; ++j) acc = fma(A[(long)j * N + r], sx[j], acc);
-      if (sg[r] >= 0) ob[sg[r]] = acc;
+      if (sg[r] >= 0) {
+        if (dd) dd[sg[r]] += omega * acc;
+        else ob[sg[r]] = acc;
+      }
     }
     __syncthreads();
   }
@@ -1561,60 +1570,74 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
   const Level& L = h->lev[l];
   MgLevelData& D = m->L[l];
   const int N = h->K1 * ne_of(h->dim);
+  const ColourMap cm = colour_map(h, L);
+  T* cb = (T*)D.cbuf;
+  const bool c13 = m->c13 && l == (int)h->lev.size() - 1;
+  const int pdisc = h->P.pressure_space == 1 ? 1 : 0;
+  VankaC13 vc;
+  memset(&vc, 0, sizeof(vc));
+  if (c13) {
+    vc.nb = m->te.nb;
+    memcpy(vc.tin, m->te.tin, sizeof(vc.tin));
+    memcpy(vc.tout, m->te.tout, sizeof(vc.tout));
+  }
+  // smoother 0: one pass over all cells into the class buffers, then
+  // d += omega sum of the buffers; smoother 1: one pass per colour class,
+  // each after a fresh defect, adding omega x into d directly
+  const bool mult = h->P.smoother == 1;
+  const int npass = mult ? cm.nclass : 1;
+  const int nt0 = N <= 128 ? 128 : 256;
+  const LaunchShape cand[5] = {{nt0, 16L * h->nsm}, {128, 16L * h->nsm}, {256, 8L * h->nsm}, {512, 4L * h->nsm},
+                               {128, 32L * h->nsm}};
+  const T om = (T)h->P.omega;
   for (int s = 0; s < sweeps; ++s) {
-    cudaError_t e = level_apply<T>(h, m, l, d, (T*)D.t2);
-    if (e != cudaSuccess) return e;
-    sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // all patches in one launch into the colour buffers, then d += omega sum;
-    // the launch shape (threads per patch CTA, CTAs per SM) is autotuned
-    const ColourMap cm = colour_map(h, L);
-    T* cb = (T*)D.cbuf;
-    const int nt0 = N <= 128 ? 128 : 256;
-    const LaunchShape cand[5] = {{nt0, 16L * h->nsm}, {128, 16L * h->nsm}, {256, 8L * h->nsm},
-                                 {512, 4L * h->nsm}, {128, 32L * h->nsm}};
-    const bool c13 = m->c13 && l == (int)h->lev.size() - 1;
-    const int pdisc = h->P.pressure_space == 1 ? 1 : 0;
-    VankaC13 vc;
-    memset(&vc, 0, sizeof(vc));
-    if (c13) {
-      vc.nb = m->te.nb;
-      memcpy(vc.tin, m->te.tin, sizeof(vc.tin));
-      memcpy(vc.tout, m->te.tout, sizeof(vc.tout));
-    }
-    auto run = [&](int i) {
-      const unsigned g = (unsigned)(L.ncells < cand[i].grid ? L.ncells : cand[i].grid);
-      const int nt = cand[i].threads;
-      if (c13) {
-        if (h->dim == 2)
-          vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
-                                                               L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1,
-                                                               L.Mv, L.Mp, pdisc);
-        else
-          vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
-                                                               L.n[0], L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1,
-                                                               L.Mv, L.Mp, pdisc);
-      } else if (h->dim == 2) {
-        vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
-                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp,
-                                                         pdisc);
-      } else {
-        vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
-                                                         L.n[1], L.n[2], cm, L.ncells, L.Nq2, L.Nq1, L.Mv, L.Mp,
-                                                         pdisc);
+    for (int c = 0; c < npass; ++c) {
+      const long li0 = mult ? cm.start[c] : 0, nli = mult ? cm.start[c + 1] - cm.start[c] : L.ncells;
+      if (nli == 0) continue;
+      cudaError_t e = level_apply<T>(h, m, l, d, (T*)D.t2);
+      if (e != cudaSuccess) return e;
+      sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      // the launch shape (threads per patch CTA, CTAs per SM) is autotuned;
+      // trial launches store into the class buffers (dd = nullptr), so they
+      // leave d alone
+      auto run = [&](int i, T* dd) {
+        const unsigned g = (unsigned)(nli < cand[i].grid ? nli : cand[i].grid);
+        const int nt = cand[i].threads;
+        if (c13) {
+          if (h->dim == 2)
+            vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+                                                                 L.n[0], L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1,
+                                                                 L.Mv, L.Mp, pdisc, dd, om);
+          else
+            vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+                                                                 L.n[0], L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1,
+                                                                 L.Mv, L.Mp, pdisc, dd, om);
+        } else if (h->dim == 2) {
+          vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+                                                           L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1, L.Mv, L.Mp,
+                                                           pdisc, dd, om);
+        } else {
+          vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+                                                           L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1, L.Mv, L.Mp,
+                                                           pdisc, dd, om);
+        }
+        return cudaGetLastError();
+      };
+      const int pick = tune_pick(std::string(c13 ? "vanka_patch_solve_c13<" : "vanka_patch_solve<") +
+                                     std::to_string(h->dim) + "," + (sizeof(T) == 8 ? "double" : "float") +
+                                     "> N=" + std::to_string(N) + " cells=" + std::to_string(nli),
+                                 5, [&](int i) { return run(i, nullptr); },
+                                 [&](int i) { return shape_label(cand[i], h->nsm); }, h->stream);
+      e = run(pick, mult ? d : nullptr);
+      if (e != cudaSuccess) return e;
+      if (!mult) {
+        colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, d, L.Nst, om, 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
       }
-      return cudaGetLastError();
-    };
-    const int pick = tune_pick(std::string(c13 ? "vanka_patch_solve_c13<" : "vanka_patch_solve<") +
-                                   std::to_string(h->dim) + "," + (sizeof(T) == 8 ? "double" : "float") +
-                                   "> N=" + std::to_string(N) + " cells=" + std::to_string(L.ncells),
-                               5, run, [&](int i) { return shape_label(cand[i], h->nsm); }, h->stream);
-    e = run(pick);
-    if (e != cudaSuccess) return e;
-    colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, d, L.Nst, (T)h->P.omega, 1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
