@@ -185,11 +185,12 @@ CONFIG3_WORKLOAD = ("3D unit cube 64^3 hexes, Q2/Q1, dG(2) 3 Radau points, dt=0.
 
 
 def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300, smoother=0, omega=None, arms=("mixed", "fp64"),
-                  dt=None):
+                  dt=None, finest=0):
     """The 64^3, dG(2) linear solve with the FP32 V-cycle (mixed) and the FP64
     V-cycle: seconds of the preconditioner set-up and of the FGMRES solve,
     iterations and final relative residual per arm."""
-    p = si.config(3, nx=mesh, ny=mesh, nz=mesh, levels=levels, coarse_solve=coarse, smoother=smoother)
+    p = si.config(3, nx=mesh, ny=mesh, nz=mesh, levels=levels, coarse_solve=coarse, smoother=smoother,
+                  finest_patches=finest)
     if omega is not None:
         p["omega"] = omega
     if dt is not None:
@@ -197,7 +198,8 @@ def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300, smoother=0,
     s = si.sizes(p)
     K1 = p["k"] + 1
     res = {"workload": CONFIG3_WORKLOAD.replace("64^3", "%d^3" % mesh), "levels": levels,
-           "coarse_solve": coarse, "smoother": smoother, "omega": p["omega"], "dt": p["dt"], "dofs": s["Nst"]}
+           "coarse_solve": coarse, "smoother": smoother, "finest_patches": finest, "omega": p["omega"], "dt": p["dt"],
+           "dofs": s["Nst"]}
     for arm, prec in (("mixed", st.ST_FP32), ("fp64", st.ST_FP64)):
         if arm not in arms:
             continue
@@ -648,6 +650,8 @@ def main():
     ap.add_argument("--config3-omega", type=float, default=None)
     ap.add_argument("--config3-dt", type=float, default=None)
     ap.add_argument("--config3-arms", default="mixed,fp64")
+    ap.add_argument("--config3-finest", type=int, default=0, choices=[0, 1],
+                    help="finest-level patches: 0 surrogate, 1 exact")
     args = ap.parse_args()
 
     p, U, dU, vp = si.workload(2)
@@ -675,7 +679,8 @@ def main():
     if args.config3_only:
         print(json.dumps(config3_solve(st, torch, args.config3_mesh, args.config3_levels, args.config3_coarse,
                                        smoother=args.config3_smoother, omega=args.config3_omega,
-                                       arms=tuple(args.config3_arms.split(",")), dt=args.config3_dt)))
+                                       arms=tuple(args.config3_arms.split(",")), dt=args.config3_dt,
+                                       finest=args.config3_finest)))
         return
     if args.batched_only:
         res = batched_comparison(st, torch)
