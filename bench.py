@@ -100,10 +100,12 @@ NEWTON_GEOMETRY = ("3D channel 4x1x1, 128x32x32 hexes, Q2/Q1, dG(1) 2 Radau poin
                    "v_prev=0; Newton to |R|_M <= 1e-8 |R0|_M (at most 30 iterations); V-cycle with 5 levels (coarsest "
                    "8x2x2), 2+2 Vanka sweeps, FP64-accurate direct coarsest solve")
 NEWTON_CASES = (
-    # (name, p, delta, start): the stated parameters from the Dirichlet lifting, and a milder
-    # (p, delta) from rest at which every arm converges (the timing comparison)
-    ("stated", 1.1, 1e-6, "lifting"),
-    ("p1.5_delta1e-3", 1.5, 1e-3, "rest"),
+    # (name, p, delta, start, solver overrides): the stated parameters from the Dirichlet lifting, and a
+    # milder (p, delta) from rest at which every arm converges (the timing comparison), with the additive
+    # Vanka step and with the colour-multiplicative one
+    ("stated", 1.1, 1e-6, "lifting", {}),
+    ("p1.5_delta1e-3", 1.5, 1e-3, "rest", {}),
+    ("p1.5_delta1e-3_colour", 1.5, 1e-3, "rest", {"smoother": 1, "omega": 0.5}),
 )
 
 
@@ -121,22 +123,29 @@ def channel_start(p, nv, torch, start):
 
 
 def newton_comparison(st, torch, mesh=(128, 32, 32), arms=("mixed", "fp64"), cases=NEWTON_CASES,
-                      tangents=("modn",), slabs=1, levels=5):
+                      tangents=("modn",), slabs=1, levels=5, maxit=30, smoother=0, omega=None):
     """Wall time of globalised Newton slab solves with the FP32 V-cycle
     (mixed) and with the FP64 V-cycle, both inside FP64 FGMRES/Newton, to the
     same relative residual 1e-8; status, iteration counts and the final
     residual (re-evaluated in FP64) per arm.  `slabs` > 1 time-marches: each
     slab starts from the previous slab's end value."""
     out = {"geometry": NEWTON_GEOMETRY.replace("128x32x32", "%dx%dx%d" % tuple(mesh)), "slabs": slabs}
+    if maxit != 30 or smoother != 0 or omega is not None:
+        out["solver"] = {"newton_maxit": maxit, "smoother": smoother, "omega": omega}
     precs = {"mixed": st.ST_FP32, "fp64": st.ST_FP64}
     tgs = {"modn": st.ST_MODN, "exn": st.ST_EXN, "pic": st.ST_PIC}
-    for name, pe, delta, start in cases:
+    for name, pe, delta, start, over in cases:
         entry = {"p": pe, "delta": delta, "start": start}
+        if over:
+            entry["solver"] = dict(over)
         for tname in tangents:
             for arm in arms:
                 prec = precs[arm]
                 p = si.config(5, nx=mesh[0], ny=mesh[1], nz=mesh[2], p=pe, delta=delta, tol_rel=1e-8,
-                              tol_abs=1e-30, newton_maxit=30, levels=levels, coarse_solve=1)
+                              tol_abs=1e-30, newton_maxit=maxit, levels=levels, coarse_solve=1, smoother=smoother)
+                if omega is not None:
+                    p["omega"] = omega
+                p.update(over)
                 prob = st.Problem(p)
                 nv = prob.velocity_size()
                 U = channel_start(p, nv, torch, start)
@@ -245,7 +254,7 @@ def batch_instances(rng):
     return plist
 
 
-def hierarchy_for(p):
+def hierarchy_for(p, smoother=0, omega=None):
     """Levels down to an odd or 2-cell coarsest mesh; the direct coarsest
     solve where that level has at most 20000 dofs."""
     n, levels = p["nx"], 1
@@ -253,10 +262,13 @@ def hierarchy_for(p):
         n //= 2
         levels += 1
     n0 = (p["k"] + 1) * (3 * (2 * n + 1) ** 3 + (n + 1) ** 3)
-    return dict(p, levels=levels, coarse_solve=1 if n0 <= 20000 else 0, coarse_sweeps=8)
+    q = dict(p, levels=levels, coarse_solve=1 if n0 <= 20000 else 0, coarse_sweeps=8, smoother=smoother)
+    if omega is not None:
+        q["omega"] = omega
+    return q
 
 
-def batched_comparison(st, torch, step=True):
+def batched_comparison(st, torch, step=True, smoother=0, omega=None):
     """Throughput of the batched operator (st_batch_jacobian_apply: one
     persistent volume launch over all instances) against the same applies
     issued instance by instance, and one modN Newton step of every instance
@@ -302,7 +314,7 @@ def batched_comparison(st, torch, step=True):
     if not step:
         return res
     # one Newton step per instance, as one batch
-    hl = [hierarchy_for(p) for p in plist]
+    hl = [hierarchy_for(p, smoother, omega) for p in plist]
     b = st.Batch(hl)
     vp = []
     for i, (p, u) in enumerate(zip(hl, U)):
@@ -319,7 +331,8 @@ def batched_comparison(st, torch, step=True):
     tstep = time.perf_counter() - t0
     conv = [inf["res_norm"] <= 1e-8 * inf["rhs_norm"] * (1 + 1e-12) for inf in infos]
     res["newton_step"] = {
-        "workload": BATCH_STEP_WORKLOAD, "seconds": tstep, "dofs": ndofs, "dofs_per_s": ndofs / tstep,
+        "workload": BATCH_STEP_WORKLOAD, "smoother": smoother, "omega": hl[0]["omega"],
+        "seconds": tstep, "dofs": ndofs, "dofs_per_s": ndofs / tstep,
         "converged": int(sum(conv)), "instances": len(hl),
         "per_instance": [{"n": p["nx"], "p": round(p["p"], 3), "delta": float("%.3g" % p["delta"]),
                           "levels": p["levels"], "coarse_solve": p["coarse_solve"], "fgmres_iters": inf["iters"],
@@ -623,6 +636,9 @@ def main():
     ap.add_argument("--newton-only", action="store_true", help="run only the Newton-step comparison and print it")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instance comparison")
     ap.add_argument("--batched-only", action="store_true", help="run only the batched-instance comparison")
+    ap.add_argument("--batched-smoother", type=int, default=0, choices=[0, 1],
+                    help="Vanka step of the batched Newton step: 0 additive, 1 colour-multiplicative")
+    ap.add_argument("--batched-omega", type=float, default=None)
     ap.add_argument("--no-cip", action="store_true", help="skip the apply with the CIP term")
     ap.add_argument("--cip-only", action="store_true", help="run only the apply with and without the CIP term")
     ap.add_argument("--sweep", action="store_true",
@@ -636,6 +652,10 @@ def main():
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--newton-levels", type=int, default=5, help="V-cycle levels of the Newton comparison")
+    ap.add_argument("--newton-maxit", type=int, default=30, help="Newton iteration cap of the comparison")
+    ap.add_argument("--newton-smoother", type=int, default=0, choices=[0, 1],
+                    help="Vanka step of the comparison: 0 additive, 1 colour-multiplicative")
+    ap.add_argument("--newton-omega", type=float, default=None)
     ap.add_argument("--newton-cases", default=",".join(c[0] for c in NEWTON_CASES),
                     help="comma list of the Newton comparison's cases (%s)" % ", ".join(c[0] for c in NEWTON_CASES))
     ap.add_argument("--newton-full", action="store_true",
@@ -670,10 +690,12 @@ def main():
         arms = tuple(args.newton_arms.split(","))
         if args.newton_full:
             res = newton_comparison(st, torch, tuple(args.newton_mesh), arms, cases=NEWTON_CASES[:1],
-                                    tangents=("modn", "exn", "pic"), slabs=5, levels=args.newton_levels)
+                                    tangents=("modn", "exn", "pic"), slabs=5, levels=args.newton_levels,
+                                    maxit=args.newton_maxit, smoother=args.newton_smoother, omega=args.newton_omega)
         else:
             cases = tuple(c for c in NEWTON_CASES if c[0] in args.newton_cases.split(","))
-            res = newton_comparison(st, torch, tuple(args.newton_mesh), arms, cases=cases, levels=args.newton_levels)
+            res = newton_comparison(st, torch, tuple(args.newton_mesh), arms, cases=cases, levels=args.newton_levels,
+                                    maxit=args.newton_maxit, smoother=args.newton_smoother, omega=args.newton_omega)
         print(json.dumps(res))
         return
     if args.config3_only:
@@ -683,7 +705,7 @@ def main():
                                        finest=args.config3_finest)))
         return
     if args.batched_only:
-        res = batched_comparison(st, torch)
+        res = batched_comparison(st, torch, smoother=args.batched_smoother, omega=args.batched_omega)
         res["autotune"] = st.autotune_report().splitlines()
         print(json.dumps(res))
         return
