@@ -1565,8 +1565,10 @@ cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
   return cudaGetLastError();
 }
 
+// d_zero: d is zero on entry (the V-cycle's pre-smoothing and coarse sweeps),
+// so the first defect is r itself and its apply is skipped
 template <typename T>
-cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r, T* d) {
+cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r, T* d, bool d_zero = false) {
   const Level& L = h->lev[l];
   MgLevelData& D = m->L[l];
   const int N = h->K1 * ne_of(h->dim);
@@ -1594,11 +1596,18 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
     for (int c = 0; c < npass; ++c) {
       const long li0 = mult ? cm.start[c] : 0, nli = mult ? cm.start[c + 1] - cm.start[c] : L.ncells;
       if (nli == 0) continue;
-      cudaError_t e = level_apply<T>(h, m, l, d, (T*)D.t2);
-      if (e != cudaSuccess) return e;
-      sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+      cudaError_t e = cudaSuccess;
+      const T* defect = (const T*)D.t;
+      if (d_zero) {
+        defect = r;  // r - A 0
+        d_zero = false;
+      } else {
+        e = level_apply<T>(h, m, l, d, (T*)D.t2);
+        if (e != cudaSuccess) return e;
+        sub_kernel<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(r, (const T*)D.t2, (T*)D.t, L.Nst);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
       // the launch shape (threads per patch CTA, CTAs per SM) is autotuned;
       // trial launches store into the class buffers (dd = nullptr), so they
       // leave d alone
@@ -1607,19 +1616,19 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
         const int nt = cand[i].threads;
         if (c13) {
           if (h->dim == 2)
-            vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+            vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, defect, cb, L.Nst,
                                                                  L.n[0], L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1,
                                                                  L.Mv, L.Mp, pdisc, dd, om);
           else
-            vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, (const T*)D.t, cb, L.Nst,
+            vanka_patch_solve_c13<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, defect, cb, L.Nst,
                                                                  L.n[0], L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1,
                                                                  L.Mv, L.Mp, pdisc, dd, om);
         } else if (h->dim == 2) {
-          vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+          vanka_patch_solve<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, defect, cb, L.Nst, L.n[0],
                                                            L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1, L.Mv, L.Mp,
                                                            pdisc, dd, om);
         } else {
-          vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, (const T*)D.t, cb, L.Nst, L.n[0],
+          vanka_patch_solve<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, defect, cb, L.Nst, L.n[0],
                                                            L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1, L.Mv, L.Mp,
                                                            pdisc, dd, om);
         }
@@ -1712,8 +1721,8 @@ cudaError_t vcycle_rec(st_problem* h, MgState* m, int l, const T* r, T* d) {
   if (l == 0)
     return h->P.coarse_solve == 1
                ? coarse_direct_solve<T>(m->cd, r, d, COARSE_REFINE_STEPS, COARSE_RTOL, h->nsm, h->stream)
-               : vanka_steps<T>(h, m, 0, h->P.coarse_sweeps, r, d);
-  e = vanka_steps<T>(h, m, l, h->P.pre_smooth, r, d);
+               : vanka_steps<T>(h, m, 0, h->P.coarse_sweeps, r, d, true);
+  e = vanka_steps<T>(h, m, l, h->P.pre_smooth, r, d, true);
   if (e != cudaSuccess) return e;
   MgLevelData& D = m->L[l];
   MgLevelData& Cd = m->L[l - 1];
