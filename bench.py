@@ -376,6 +376,14 @@ def perf_profile(W, taus):
     return [[float(np.mean(r[:, s] <= t)) for t in taus] for s in range(W.shape[1])]
 
 
+def failure_kind(st, status, newton_iters, newton_maxit):
+    """Why a slab's Newton solve stopped: the Armijo search hit lambda_min,
+    the iteration cap was reached, or a linear solve missed its forcing."""
+    if status == st.ST_LINESEARCH_FAILED:
+        return "linesearch"
+    return "newton_cap" if newton_iters >= newton_maxit else "linear"
+
+
 def sweep_instance(st, torch, p, tangent, slabs, vprec):
     """Time-march `slabs` slabs with one Newton step each; returns the Newton
     counts per slab, the FGMRES iterations and the work, or the failure."""
@@ -389,9 +397,8 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
     for _ in range(slabs):
         status, info = prob.newton_step(tangent, U, vprev, vcycle_prec=vprec, raise_on_fail=False)
         if status != st.ST_OK:
-            kind = ("linesearch" if status == st.ST_LINESEARCH_FAILED else
-                    "newton_cap" if info["newton_iters"] >= p["newton_maxit"] else "linear")
-            fail = {"slab": len(n_nl), "kind": kind, "newton_iters": info["newton_iters"],
+            fail = {"slab": len(n_nl), "kind": failure_kind(st, status, info["newton_iters"], p["newton_maxit"]),
+                    "newton_iters": info["newton_iters"],
                     "fgmres_iters": info["fgmres_iters_total"],
                     "res_ratio": info["res_norm_final"] / max(info["res_norm_initial"], 1e-300)}
             break

@@ -38,3 +38,10 @@ def test_profile_properties_on_random_tables():
     wins = (W == W.min(axis=1, keepdims=True)) & np.isfinite(W)
     np.testing.assert_allclose(prof[:, 0], wins.mean(axis=0))       # pi_s(1): share of (tied) wins
     np.testing.assert_allclose(prof[:, -1], np.isfinite(W).mean(axis=0))  # large tau: share solved
+
+
+def test_failure_kind_names_the_stopping_cause():
+    import paper_2603_28706_gb300 as st
+    assert bench.failure_kind(st, st.ST_LINESEARCH_FAILED, 3, 30) == "linesearch"
+    assert bench.failure_kind(st, st.ST_NOT_CONVERGED, 30, 30) == "newton_cap"
+    assert bench.failure_kind(st, st.ST_NOT_CONVERGED, 2, 30) == "linear"
