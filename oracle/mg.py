@@ -10,6 +10,12 @@ restatement on the oracle's assembled matrices, small meshes only:
   galerkin           A_l = P^T A_{l+1} P (Petrov-Galerkin with Pi = P^T)
   patch_dofs         cell patch K: every velocity and pressure dof of cell K at
                      every Radau node (the full time-step block)
+  vertex_patch_dofs  vertex-star patch of vertex v (patches="vertex"): the
+                     velocity nodes of the cells around v that are not on
+                     the star's outer boundary (Q2 indices 2 v_a - 1 .. 2 v_a
+                     + 1 per axis, clipped to the mesh, so nodes on the domain
+                     boundary belong to it), the pressure at v, every Radau
+                     node; vertex classes by vertex parity
   exact_patch        A_{l,K} = R_K A_l R_K^T
   surrogate_operator finest level: the slab operator with every node's state
                      replaced by u_rep = sum_mu l_mu(t_rep) V_mu, t_rep the slab
@@ -154,6 +160,42 @@ def surrogate_operator(p, var, U):
     return assemble_csr(p, var, rep_state(p, U))
 
 
+def vertex_patch_dofs(p):
+    """Dofs of the vertex-star patch of every vertex (lexicographic, x fastest):
+    per Radau node mu the velocity components c, the patch's Q2 nodes
+    lexicographically, then the pressure at the vertex."""
+    s = sizes(p)
+    d, K1 = p["dim"], p["k"] + 1
+    n = [p["nx"], p["ny"], p["nz"] if d == 3 else 0]
+    g2 = [2 * n[0] + 1, 2 * n[1] + 1, 2 * n[2] + 1]
+    g1 = [n[0] + 1, n[1] + 1, n[2] + 1]
+    out = []
+    for vz in range(g1[2]):
+        for vy in range(g1[1]):
+            for vx in range(g1[0]):
+                v = (vx, vy, vz)
+                rng = [[i for i in (2 * v[a] - 1, 2 * v[a], 2 * v[a] + 1) if 0 <= i < g2[a]] for a in range(3)]
+                nodes = [ix + g2[0] * (iy + g2[1] * iz) for iz in rng[2] for iy in rng[1] for ix in rng[0]]
+                pv = vx + g1[0] * (vy + g1[1] * vz)
+                dofs = []
+                for mu in range(K1):
+                    for c in range(d):
+                        dofs += [mu * s["Mv"] + c * s["Nq2"] + g for g in nodes]
+                    dofs.append(K1 * s["Mv"] + mu * s["Mp"] + pv)
+                out.append(np.array(dofs, dtype=np.int64))
+    return out
+
+
+def vertex_classes(p):
+    """Vertices of each class px + 2 py + 4 pz of vertex-coordinate parities;
+    the patches of two vertices of one class share no dof."""
+    d = p["dim"]
+    g1 = [p["nx"] + 1, p["ny"] + 1, (p["nz"] + 1) if d == 3 else 1]
+    v = np.arange(g1[0] * g1[1] * g1[2])
+    cls = (v % g1[0]) % 2 + 2 * (((v // g1[0]) % g1[1]) % 2) + 4 * ((v // (g1[0] * g1[1])) % 2)
+    return [np.where(cls == k)[0] for k in range(2 ** d)]
+
+
 def colour_classes(p):
     """Cells of each colour class, class px + 2 py + 4 pz holding the cells
     whose coordinates (x fastest in the linear cell index) have parities
@@ -187,13 +229,20 @@ class Hierarchy:
     (the refresh rule of Sec. 6.3 keeps them otherwise)."""
 
     def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True,
-                 coarse_solve="sweeps", smoother="additive"):
+                 coarse_solve="sweeps", smoother="additive", patches="cell"):
         if coarse_solve not in ("sweeps", "direct"):
             raise ValueError("coarse_solve must be 'sweeps' or 'direct'")
         if smoother not in ("additive", "colour"):
             raise ValueError("smoother must be 'additive' or 'colour'")
+        if patches not in ("cell", "vertex"):
+            raise ValueError("patches must be 'cell' or 'vertex'")
+        if patches == "vertex" and surrogate:
+            raise ValueError("vertex-star patches are exact patches (surrogate=False)")
+        if patches == "vertex" and p.get("pressure_space", 0) != 0:
+            raise ValueError("vertex-star patches carry the Q1 vertex pressure (pressure_space = 0)")
         self.p, self.levels = p, levels
         self.smoother = smoother
+        self.patches = patches
         self.coarse_solve = coarse_solve
         self.lu0 = None
         self.omega = omega
@@ -203,7 +252,10 @@ class Hierarchy:
         self.P = [None] * levels  # P[l]: level l-1 -> level l
         for l in range(levels - 1, 0, -1):
             self.P[l] = prolongation(self.params[l - 1])
-        self.dofs = [cell_dofs(pl, np.arange(sizes(pl)["ncells"])) for pl in self.params]
+        if patches == "vertex":
+            self.dofs = [vertex_patch_dofs(pl) for pl in self.params]
+        else:
+            self.dofs = [cell_dofs(pl, np.arange(sizes(pl)["ncells"])) for pl in self.params]
         self.A = [None] * levels
         self.Afine = None  # finest-level operator of the defects (with CIP)
         self.Ainv = [None] * levels
@@ -233,7 +285,8 @@ class Hierarchy:
     def vanka_step(self, l, r, d):
         A = self.op(l)
         if self.smoother == "colour":
-            return colour_sweep(A, self.Ainv[l], self.dofs[l], colour_classes(self.params[l]), self.omega, r, d)
+            cls = vertex_classes(self.params[l]) if self.patches == "vertex" else colour_classes(self.params[l])
+            return colour_sweep(A, self.Ainv[l], self.dofs[l], cls, self.omega, r, d)
         defect = r - A @ d
         corr = np.zeros_like(d)
         for c, dof in enumerate(self.dofs[l]):
