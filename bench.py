@@ -414,7 +414,9 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
 def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=None, smoother="additive"):
     """Analogue of the solver evaluation of Sec. 7 (Table newton-compact, eq.
     work, eq. perf-profile) on synthetic channel problems: every (p, delta,
-    mesh) instance with Pic, exN and modN."""
+    mesh) instance with Pic, exN and modN.  patches: "surrogate" or "exact"
+    cell patches on the finest level, or "vertex" (exact vertex-star patches
+    on every level)."""
     tangents = {"Pic": st.ST_PIC, "exN": st.ST_EXN, "modN": st.ST_MODN}
     vprec = st.ST_FP32 if vprec_name == "fp32" else st.ST_FP64
     inst, W = [], []
@@ -427,7 +429,8 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=No
                                      nu=1e-3, nu_inf=0.0, sigma_max=1e-4, inflow_profile=1, vbar=0.1,
                                      levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30,
                                      finest_patches=0 if patches == "surrogate" else 1,
-                                     smoother=0 if smoother == "additive" else 1)
+                                     smoother=0 if smoother == "additive" else 1,
+                                     patch_type=1 if patches == "vertex" else 0)
                 if omega is not None:
                     prm["omega"] = omega
                 row = {"cells": 4 * n * n, "p": pe, "delta": delta}
@@ -651,8 +654,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="run only the robustness sweep (Pic / exN / modN over (p, delta, mesh)) and print it")
     ap.add_argument("--sweep-vcycle", default="fp32", choices=["fp32", "fp64"], help="V-cycle precision of the sweep")
-    ap.add_argument("--sweep-patches", default="surrogate", choices=["surrogate", "exact"],
-                    help="finest-level Vanka patches of the sweep: the surrogate of eq. surrogate-diag or exact")
+    ap.add_argument("--sweep-patches", default="surrogate", choices=["surrogate", "exact", "vertex"],
+                    help="Vanka patches of the sweep: cell patches with the surrogate of eq. surrogate-diag or "
+                         "exact on the finest level, or exact vertex-star patches")
     ap.add_argument("--sweep-omega", type=float, default=None, help="Vanka damping of the sweep (default: 2D default)")
     ap.add_argument("--sweep-smoother", default="additive", choices=["additive", "colour"],
                     help="Vanka step of the sweep: additive (eq. stmg-vanka-update) or colour-multiplicative")

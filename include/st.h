@@ -114,6 +114,13 @@ typedef struct {
                                  defect before each class: multiplicative between
                                  classes, additive inside one (its cells share no
                                  dof); 2^dim defects per step                        */
+  int patch_type;             /* Vanka patches (Sec. 6.3): 0 = cell patches (every dof
+                                 of a cell); 1 = vertex-star patches: the velocity
+                                 nodes of the 2^dim cells around a vertex that are not
+                                 on the star's outer boundary, and the vertex's
+                                 pressure, all k+1 time nodes, classes by vertex
+                                 parity; exact patches only (finest_patches = 1,
+                                 gamma_cip = 0, pressure_space = 0)                  */
 } st_params;
 
 typedef struct {

@@ -245,6 +245,10 @@ st_status check_params(const st_params& P, std::string& why) {
   if (P.coarse_solve != 0 && P.coarse_solve != 1) return why = "coarse_solve must be 0 or 1", ST_EINVAL;
   if (P.pressure_space != 0 && P.pressure_space != 1) return why = "pressure_space must be 0 or 1", ST_EINVAL;
   if (P.smoother != 0 && P.smoother != 1) return why = "smoother must be 0 or 1", ST_EINVAL;
+  if (P.patch_type != 0 && P.patch_type != 1) return why = "patch_type must be 0 or 1", ST_EINVAL;
+  if (P.patch_type == 1 && (P.finest_patches != 1 || P.gamma_cip > 0 || P.pressure_space != 0))
+    return why = "patch_type = 1 (vertex-star patches) needs finest_patches = 1, gamma_cip = 0 and pressure_space = 0",
+           ST_EINVAL;
   if (P.coarse_solve == 1) {
     long n2 = 1, n1 = 1;
     const int nn[3] = {P.nx, P.ny, P.dim == 3 ? P.nz : 0};

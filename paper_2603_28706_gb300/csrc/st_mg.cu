@@ -39,6 +39,10 @@ namespace {
 constexpr int MAXN = 4 * 89;  // largest patch size (k = 3, 3D)
 
 int ne_of(int dim) { return dim == 3 ? 3 * 27 + 8 : 2 * 9 + 4; }
+// vertex-star patch dofs per time node: the 3^dim velocity nodes around the
+// vertex (every component) and its pressure
+int nev_of(int dim) { return dim == 3 ? 3 * 27 + 1 : 2 * 9 + 1; }
+long n_vertices(const st_problem* h, const Level& L);
 
 // ------------------------------------------------------------- transfers
 // One direction of the nested prolongation on blocks of a tensor grid:
@@ -415,6 +419,100 @@ __global__ void patch_assemble(const T* __restrict__ E, int estride, PatchArgs p
           if (vel_pair) v += (T)(pa.Kt[mu * K1 + nu] * mass);
           // column-major: F[col][row]
           Fk[(long)(nu * NE + q) * N + (mu * NE + p)] = v;
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// Vertex-star patch of vertex v (patch_type = 1, exact patches only): per
+// time node the velocity nodes with Q2 indices 2 v_a - 1 + j_a, j in {0,1,2}^d,
+// that lie in the mesh (every component), then the pressure at v.  The spatial
+// block sums the element matrices E[e][mu] of the 2^d cells e = v - 1 + o,
+// o in {0,1}^d, around v; patch node j is local node j_a + 1 - 2 o_a of cell e
+// and the vertex is local Q1 node 1 - o_a.  Dofs outside the mesh get an
+// identity row and column.  Column-major F[col][row] as for cell patches.
+template <int DIM>
+__device__ __forceinline__ bool vertex_local(int dof, const int o[3], int& out) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM;
+  if (dof == NC * NQ) {
+    out = NC * NQ + (1 - o[0]) + 2 * (1 - o[1]) + (DIM == 3 ? 4 * (1 - o[2]) : 0);
+    return true;
+  }
+  const int c = dof / NQ, n = dof % NQ;
+  const int j[3] = {n % 3, (n / 3) % 3, n / 9};
+  int l[3] = {0, 0, 0};
+  for (int d = 0; d < DIM; ++d) {
+    l[d] = j[d] + 1 - 2 * o[d];
+    if (l[d] < 0 || l[d] > 2) return false;
+  }
+  out = c * NQ + l[0] + 3 * l[1] + 9 * l[2];
+  return true;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool vertex_dof_in_mesh(int dof, const int v[3], const int n[3]) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM;
+  if (dof == NC * NQ) return true;
+  const int q = dof % NQ;
+  const int j[3] = {q % 3, (q / 3) % 3, q / 9};
+  for (int d = 0; d < DIM; ++d) {
+    const int gi = 2 * v[d] - 1 + j[d];
+    if (gi < 0 || gi > 2 * n[d]) return false;
+  }
+  return true;
+}
+
+template <int DIM, typename T>
+__global__ void patch_assemble_vertex(const T* __restrict__ E, int estride, PatchArgs pa, T* __restrict__ F) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NE = NC * NQ + (DIM == 3 ? 8 : 4), NEV = NC * NQ + 1;
+  const int K1 = pa.K1, N = K1 * NEV;
+  const int nv0 = pa.n[0] + 1, nv1 = pa.n[1] + 1;
+  const long nvert = (long)nv0 * nv1 * (DIM == 3 ? pa.n[2] + 1 : 1);
+  __shared__ double smass[NQ * NQ];
+  for (int t = threadIdx.x; t < NQ * NQ; t += blockDim.x) {
+    const int a = t / NQ, b = t % NQ;
+    const int ai[3] = {a % 3, (a / 3) % 3, a / 9}, bi[3] = {b % 3, (b / 3) % 3, b / 9};
+    double m = 1.0;
+    for (int d = 0; d < DIM; ++d) m *= pa.M1h[d][ai[d] * 3 + bi[d]];
+    smass[t] = m;
+  }
+  __syncthreads();
+  for (long V = blockIdx.x; V < nvert; V += gridDim.x) {
+    const int v[3] = {(int)(V % nv0), (int)((V / nv0) % nv1), DIM == 3 ? (int)(V / ((long)nv0 * nv1)) : 0};
+    T* Fv = F + V * (long)N * N;
+    for (int it = threadIdx.x; it < NEV * NEV; it += blockDim.x) {
+      const int p = it / NEV, q = it % NEV;  // row, column within a spatial block
+      const bool inp = vertex_dof_in_mesh<DIM>(p, v, pa.n), inq = vertex_dof_in_mesh<DIM>(q, v, pa.n);
+      const bool vel_pair = p < NC * NQ && q < NC * NQ && (p / NQ) == (q / NQ);
+      T S[4] = {0, 0, 0, 0};
+      double mass = 0.0;
+      if (inp && inq) {
+        for (int oc = 0; oc < (1 << DIM); ++oc) {
+          const int o[3] = {oc & 1, (oc >> 1) & 1, (oc >> 2) & 1};
+          int e3[3] = {0, 0, 0};
+          bool inside = true;
+          for (int d = 0; d < DIM; ++d) {
+            e3[d] = v[d] - 1 + o[d];
+            inside = inside && e3[d] >= 0 && e3[d] < pa.n[d];
+          }
+          int lp, lq;
+          if (!inside || !vertex_local<DIM>(p, o, lp) || !vertex_local<DIM>(q, o, lq)) continue;
+          const long ecell = e3[0] + (long)pa.n[0] * (e3[1] + (long)pa.n[1] * e3[2]);
+          for (int mu = 0; mu < K1; ++mu) S[mu] += E[(ecell * estride + mu) * NE * NE + (long)lp * NE + lq];
+          if (vel_pair) mass += smass[(lp % NQ) * NQ + (lq % NQ)];
+        }
+      }
+      for (int mu = 0; mu < K1; ++mu)
+        for (int nu = 0; nu < K1; ++nu) {
+          T val;
+          if (inp && inq) {
+            val = (mu == nu) ? S[mu] : (T)0;
+            if (vel_pair) val += (T)(pa.Kt[mu * K1 + nu] * mass);
+          } else {
+            val = (mu == nu && p == q) ? (T)1 : (T)0;
+          }
+          Fv[(long)(nu * NEV + q) * N + (mu * NEV + p)] = val;
         }
     }
     __syncthreads();
@@ -1177,6 +1275,60 @@ __global__ void vanka_patch_solve(const T* __restrict__ F, int K1, const T* __re
   }
 }
 
+// Vertex-star patch solves of the colour-ordered vertices li0 .. li0 + nli - 1
+// (vm: classes of vertex parities over the (n + 1)^d vertex grid), as
+// vanka_patch_solve: into the class buffers, or omega x added into dd.
+template <int DIM, typename T>
+__global__ void vanka_patch_solve_vertex(const T* __restrict__ F, int K1, const T* __restrict__ defect,
+                                         T* __restrict__ cb, long cstride, int n0, int n1, int n2, ColourMap vm,
+                                         long li0, long nli, long Nq2, long Mv, long Mp, T* __restrict__ dd,
+                                         T omega) {
+  constexpr int NQ = DIM == 3 ? 27 : 9, NC = DIM, NEV = NC * NQ + 1;
+  const int N = K1 * NEV;
+  __shared__ T sx[MAXN];
+  __shared__ long sg[MAXN];
+  const long g2x = 2L * n0 + 1, g2y = 2L * n1 + 1, g1x = (long)n0 + 1, g1y = (long)n1 + 1;
+  const int nn[3] = {n0, n1, n2};
+  for (long li = li0 + blockIdx.x; li < li0 + nli; li += gridDim.x) {
+    int col, vx, vy, vz;
+    colour_cell(vm, li, col, vx, vy, vz);
+    const long V = vx + g1x * (vy + g1y * (long)vz);
+    T* ob = cb + col * cstride;
+    const T* A = F + V * (long)N * N;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int mu = r / NEV, loc = r % NEV;
+      long g;
+      if (loc < NC * NQ) {
+        const int c = loc / NQ, q = loc % NQ;
+        const int v3[3] = {vx, vy, vz};
+        const int j[3] = {q % 3, (q / 3) % 3, q / 9};
+        long gi[3] = {0, 0, 0};
+        bool in = true;
+        for (int d = 0; d < DIM; ++d) {
+          gi[d] = 2L * v3[d] - 1 + j[d];
+          in = in && gi[d] >= 0 && gi[d] <= 2L * nn[d];
+        }
+        g = in ? (long)mu * Mv + c * Nq2 + gi[0] + g2x * (gi[1] + g2y * gi[2]) : -1;
+      } else {
+        g = (long)K1 * Mv + (long)mu * Mp + vx + g1x * (vy + g1y * (long)vz);
+      }
+      sg[r] = g;
+      sx[r] = g >= 0 ? defect[g] : (T)0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      T acc = 0;
+#pragma unroll 8
+      for (int j = 0; j < N; ++j) acc = fma(A[(long)j * N + r], sx[j], acc);
+      if (sg[r] >= 0) {
+        if (dd) dd[sg[r]] += omega * acc;
+        else ob[sg[r]] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------- coarse-level apply
 // (A_l x)|_K for all cells in one launch, into the buffer of the cell's
 // colour class: per cell and node mu the element matrix E[cell][mu] (spatial
@@ -1335,6 +1487,7 @@ struct MgLevelData {
   void* t2 = nullptr;
   void* t3 = nullptr;
   void* cbuf = nullptr;  // 2^d colour-private level vectors (zero outside each class's dofs)
+  void* vbuf = nullptr;  // the same for the vertex-star patches' classes (patch_type = 1)
 };
 
 struct MgState {
@@ -1387,6 +1540,7 @@ void free_mg(MgState* m) {
     cudaFree(l.t2);
     cudaFree(l.t3);
     cudaFree(l.cbuf);
+    cudaFree(l.vbuf);
   }
   m->L.clear();
   cudaFree(m->Erep);
@@ -1421,8 +1575,14 @@ cudaError_t alloc_mg(st_problem* h, MgState* m, int prec) {
     // finest level with the time-diagonalised surrogate: nb complex NE x NE inverses per patch
     const bool c13 = (l == nl - 1) && m->c13;
     const size_t nlu = c13 ? (size_t)m->te.nb * NE * NE * 2 : (size_t)N * N;
-    if (e == cudaSuccess) e = cudaMalloc(&d.LU, (size_t)Lv.ncells * nlu * es);
-    if (e == cudaSuccess) e = cudaMalloc(&d.piv, (size_t)Lv.ncells * N * sizeof(int));
+    // vertex-star patches: one K1 * nev_of(dim) patch per vertex
+    const bool vtx = h->P.patch_type == 1;
+    const size_t Nv = (size_t)K1 * nev_of(h->dim);
+    const size_t npat = vtx ? (size_t)n_vertices(h, Lv) : (size_t)Lv.ncells;
+    if (e == cudaSuccess) e = cudaMalloc(&d.LU, npat * (vtx ? Nv * Nv : nlu) * es);
+    if (e == cudaSuccess) e = cudaMalloc(&d.piv, npat * (vtx ? Nv : (size_t)N) * sizeof(int));
+    if (e == cudaSuccess && vtx) e = cudaMalloc(&d.vbuf, (size_t)(1 << h->dim) * Lv.Nst * es);
+    if (e == cudaSuccess && vtx) e = cudaMemset(d.vbuf, 0, (size_t)(1 << h->dim) * Lv.Nst * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.r, (size_t)Lv.Nst * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.d, (size_t)Lv.Nst * es);
     if (e == cudaSuccess) e = cudaMalloc(&d.t, (size_t)Lv.Nst * es);
@@ -1528,6 +1688,29 @@ ColourMap colour_map(const st_problem* h, const Level& L) {
   return cm;
 }
 
+long n_vertices(const st_problem* h, const Level& L) {
+  return (long)(L.n[0] + 1) * (L.n[1] + 1) * (h->dim == 3 ? L.n[2] + 1 : 1);
+}
+
+// classes of the vertex grid by vertex-coordinate parity (px + 2 py + 4 pz),
+// in the ColourMap form the patch kernels read
+ColourMap vertex_map(const st_problem* h, const Level& L) {
+  ColourMap cm;
+  cm.nclass = 1 << h->dim;
+  long start = 0;
+  for (int c = 0; c < 8; ++c) {
+    cm.start[c] = start;
+    for (int a = 0; a < 3; ++a) {
+      const int nv = a < h->dim ? L.n[a] + 1 : 1, bit = a < h->dim ? (c >> a) & 1 : 0;
+      cm.cn[c][a] = (nv + 1 - bit) / 2;
+    }
+    if (c < cm.nclass) start += (long)cm.cn[c][0] * cm.cn[c][1] * cm.cn[c][2];
+  }
+  cm.start[8] = start;
+  for (int c = cm.nclass; c < 8; ++c) cm.start[c] = start;
+  return cm;
+}
+
 template <typename T>
 cudaError_t level_apply(st_problem* h, MgState* m, int l, const T* x, T* y) {
   // y = A_l x
@@ -1588,13 +1771,19 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
   // each after a fresh defect, adding omega x into d directly
   const bool mult = h->P.smoother == 1;
   const int npass = mult ? cm.nclass : 1;
-  const int nt0 = N <= 128 ? 128 : 256;
+  // vertex-star patches (patch_type = 1): their own classes and buffers
+  const bool vtx = h->P.patch_type == 1;
+  const ColourMap pm = vtx ? vertex_map(h, L) : cm;
+  const long npatch = vtx ? n_vertices(h, L) : L.ncells;
+  T* pbuf = vtx ? (T*)D.vbuf : cb;
+  const int Np = vtx ? h->K1 * nev_of(h->dim) : N;
+  const int nt0 = Np <= 128 ? 128 : 256;
   const LaunchShape cand[5] = {{nt0, 16L * h->nsm}, {128, 16L * h->nsm}, {256, 8L * h->nsm}, {512, 4L * h->nsm},
                                {128, 32L * h->nsm}};
   const T om = (T)h->P.omega;
   for (int s = 0; s < sweeps; ++s) {
     for (int c = 0; c < npass; ++c) {
-      const long li0 = mult ? cm.start[c] : 0, nli = mult ? cm.start[c + 1] - cm.start[c] : L.ncells;
+      const long li0 = mult ? pm.start[c] : 0, nli = mult ? pm.start[c + 1] - pm.start[c] : npatch;
       if (nli == 0) continue;
       cudaError_t e = cudaSuccess;
       const T* defect = (const T*)D.t;
@@ -1614,7 +1803,16 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
       auto run = [&](int i, T* dd) {
         const unsigned g = (unsigned)(nli < cand[i].grid ? nli : cand[i].grid);
         const int nt = cand[i].threads;
-        if (c13) {
+        if (vtx) {
+          if (h->dim == 2)
+            vanka_patch_solve_vertex<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, defect, pbuf, L.Nst,
+                                                                    L.n[0], L.n[1], L.n[2], pm, li0, nli, L.Nq2,
+                                                                    L.Mv, L.Mp, dd, om);
+          else
+            vanka_patch_solve_vertex<3, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, h->K1, defect, pbuf, L.Nst,
+                                                                    L.n[0], L.n[1], L.n[2], pm, li0, nli, L.Nq2,
+                                                                    L.Mv, L.Mp, dd, om);
+        } else if (c13) {
           if (h->dim == 2)
             vanka_patch_solve_c13<2, T><<<g, nt, 0, h->stream>>>((const T*)D.LU, vc, h->K1, defect, cb, L.Nst,
                                                                  L.n[0], L.n[1], L.n[2], cm, li0, nli, L.Nq2, L.Nq1,
@@ -1634,15 +1832,17 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
         }
         return cudaGetLastError();
       };
-      const int pick = tune_pick(std::string(c13 ? "vanka_patch_solve_c13<" : "vanka_patch_solve<") +
+      const int pick = tune_pick(std::string(vtx ? "vanka_patch_solve_vertex<"
+                                                 : c13 ? "vanka_patch_solve_c13<" : "vanka_patch_solve<") +
                                      std::to_string(h->dim) + "," + (sizeof(T) == 8 ? "double" : "float") +
-                                     "> N=" + std::to_string(N) + " cells=" + std::to_string(nli),
+                                     "> N=" + std::to_string(Np) + (vtx ? " vertices=" : " cells=") +
+                                     std::to_string(nli),
                                  5, [&](int i) { return run(i, nullptr); },
                                  [&](int i) { return shape_label(cand[i], h->nsm); }, h->stream);
       e = run(pick, mult ? d : nullptr);
       if (e != cudaSuccess) return e;
       if (!mult) {
-        colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(cb, L.Nst, cm.nclass, d, L.Nst, om, 1);
+        colour_sum<T><<<gridn(L.Nst, h->nsm), 256, 0, h->stream>>>(pbuf, L.Nst, cm.nclass, d, L.Nst, om, 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -1859,6 +2059,35 @@ st_status mg_setup(st_problem* h, st_prec prec, bool rebuild_finest) {
     const Level& Lv = h->lev[l];
     const bool sur = (l == L) && !exact_finest;
     if (l == L && !rebuild_finest) continue;  // refresh rule: keep the finest factorisations
+    if (h->P.patch_type == 1) {
+      // vertex-star patches from the level's exact element matrices
+      const long nvx = n_vertices(h, Lv);
+      const int Nv = K1 * nev_of(h->dim);
+      const unsigned gv = (unsigned)(nvx < 8L * h->nsm ? nvx : 8L * h->nsm);
+      const PatchArgs pv = patch_args(h, l, false);
+      if (prec == ST_FP64) {
+        if (h->dim == 2)
+          patch_assemble_vertex<2, double><<<gv, 256, 0, h->stream>>>((const double*)m->L[l].E, K1, pv,
+                                                                      (double*)m->L[l].LU);
+        else
+          patch_assemble_vertex<3, double><<<gv, 256, 0, h->stream>>>((const double*)m->L[l].E, K1, pv,
+                                                                      (double*)m->L[l].LU);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+          e = invert_patches<double>((double*)m->L[l].LU, m->L[l].piv, Nv, nvx, h->d_err, h->nsm, h->stream);
+      } else {
+        if (h->dim == 2)
+          patch_assemble_vertex<2, float><<<gv, 256, 0, h->stream>>>((const float*)m->L[l].E, K1, pv,
+                                                                     (float*)m->L[l].LU);
+        else
+          patch_assemble_vertex<3, float><<<gv, 256, 0, h->stream>>>((const float*)m->L[l].E, K1, pv,
+                                                                     (float*)m->L[l].LU);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+          e = invert_patches<float>((float*)m->L[l].LU, m->L[l].piv, Nv, nvx, h->d_err, h->nsm, h->stream);
+      }
+      continue;
+    }
     PatchArgs pa = patch_args(h, l, sur);
     const bool c13 = sur && m->c13;
     if (c13) {

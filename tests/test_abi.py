@@ -42,7 +42,10 @@ def test_setup_rejects_bad_parameters_without_gpu():
     h = ctypes.c_void_p()
     for bad in (dict(dim=4), dict(p=2.5), dict(k=7), dict(levels=3, nx=6), dict(delta=0.0), dict(nx=0),
                 dict(gamma_cip=-1.0), dict(finest_patches=2), dict(finest_patches=1, gamma_cip=1.0),
-                dict(coarse_solve=2), dict(coarse_solve=1, nx=16, ny=16, nz=16, levels=1), dict(pressure_space=2), dict(smoother=2)):
+                dict(coarse_solve=2), dict(coarse_solve=1, nx=16, ny=16, nz=16, levels=1), dict(pressure_space=2),
+                dict(smoother=2), dict(patch_type=2),
+                dict(patch_type=1, finest_patches=0), dict(patch_type=1, finest_patches=1, gamma_cip=0.5),
+                dict(patch_type=1, finest_patches=1, pressure_space=1)):
         P = st.params(si.base_params(**bad))
         assert lib.st_setup_mesh(ctypes.byref(P), None, ctypes.byref(h)) == st.ST_EINVAL
     assert lib.st_setup_mesh(None, None, ctypes.byref(h)) == st.ST_EINVAL
@@ -70,6 +73,7 @@ def test_binding_carries_the_optional_fields():
     P = st.params(si.base_params(gamma_cip=0.5, finest_patches=0, pressure_space=1, coarse_solve=1, smoother=1))
     assert P.gamma_cip == 0.5 and P.finest_patches == 0 and P.pressure_space == 1 and P.coarse_solve == 1
     assert P.smoother == 1
+    assert st.params(si.base_params(patch_type=1)).patch_type == 1
     # the allocation-free mass norm implements the Q2/Q1 pair only
     with pytest.raises(ValueError):
         st.mnorm_noalloc(si.base_params(pressure_space=1), None)

@@ -1,0 +1,103 @@
+"""Parity of the vertex-star Vanka patches (patch_type = 1) with the oracle
+hierarchy (patches="vertex"): Vanka steps on one level with the additive and
+the colour-multiplicative step, V-cycles (eager and graph replay, FP64 and
+FP32) and a Newton solve.  Tolerances as for cell patches: FP64 1e-9, FP32 1e-3
+of max|oracle| (single-precision explicit-inverse patch solves)."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.krylov as kr
+import oracle.mg as mg
+import st_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-9, 1e-3
+VAR = {0: oracle.PIC, 1: oracle.EXN, 2: oracle.MODN}
+SMOOTHER = {0: "additive", 1: "colour"}
+
+
+def gpu():
+    import paper_2603_28706_gb300 as st
+    return st
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def rel(g, ref):
+    return np.abs(g.detach().double().cpu().numpy() - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=3, ny=2, k=1), dict(dim=2, nx=1, ny=1, k=2, inflow_profile=1),
+                                  dict(dim=3, nx=2, ny=2, nz=1, k=1), dict(dim=3, nx=1, ny=2, nz=1, k=0),
+                                  dict(dim=3, nx=1, ny=1, nz=1, k=2)])
+@pytest.mark.parametrize("sm", [0, 1])
+def test_vertex_vanka_steps(case, sm):
+    om = 0.3 if sm == 0 else 0.6
+    p = si.base_params(p=1.5, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, levels=1, smoother=sm, omega=om,
+                       patch_type=1, finest_patches=1, **case)
+    st = gpu()
+    U = si.fourier_state(p, 0)
+    s = oracle.sizes(p)
+    r = si.uniform(s["Nst"], 1)
+    d0 = 0.1 * si.uniform(s["Nst"], 2)
+    H = mg.Hierarchy(p, oracle.MODN, U, 1, om, 1, 1, surrogate=False, smoother=SMOOTHER[sm], patches="vertex")
+    ref = H.smooth(0, r, d0.copy(), 2)
+    prob = st.Problem(p)
+    prob.linearize(st.ST_MODN, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        d = dev(d0, dt)
+        prob.vanka_smooth(0, 2, dev(r, dt), d, prec=prec)
+        assert rel(d, ref) <= tol, (prec, rel(d, ref))
+    prob.close()
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=8, ny=4, k=1, levels=3, inflow_profile=1),
+                                  dict(dim=3, nx=4, ny=2, nz=2, k=1, levels=2)])
+@pytest.mark.parametrize("sm", [0, 1])
+def test_vertex_vcycle(case, sm):
+    om = 0.3 if sm == 0 else 0.6
+    p = si.base_params(p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, coarse_sweeps=3, smoother=sm,
+                       omega=om, patch_type=1, finest_patches=1, **case)
+    st = gpu()
+    U = si.fourier_state(p, 0)
+    r = si.uniform(oracle.sizes(p)["Nst"], 1)
+    H = mg.Hierarchy(p, VAR[2], U, p["levels"], om, p["pre_smooth"], p["post_smooth"],
+                     coarse_sweeps=p["coarse_sweeps"], surrogate=False, smoother=SMOOTHER[sm], patches="vertex")
+    ref = H.vcycle(r)
+    Hc = mg.Hierarchy(p, VAR[2], U, p["levels"], om, p["pre_smooth"], p["post_smooth"],
+                      coarse_sweeps=p["coarse_sweeps"], surrogate=False, smoother=SMOOTHER[sm])
+    assert np.abs(Hc.vcycle(r) - ref).max() > 1e-6 * np.abs(ref).max()  # differs from cell patches
+    prob = st.Problem(p)
+    prob.linearize(2, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        for _ in range(2):  # eager, then the captured graph
+            d = prob.vcycle(dev(r, dt), prec=prec)
+            assert rel(d, ref) <= tol, (prec, rel(d, ref))
+    prob.close()
+
+
+def test_vertex_newton_matches_oracle():
+    n = 8
+    p = si.base_params(dim=2, nx=4 * n, ny=n, Lx=4.0, Ly=1.0, k=1, dt=1.0, p=1.5, delta=1e-5, nu=1e-3, nu_inf=0.0,
+                       sigma_max=1e-4, inflow_profile=1, vbar=0.1, levels=3, tol_rel=1e-8, tol_abs=1e-30,
+                       finest_patches=1, smoother=1, omega=0.5, coarse_solve=1, patch_type=1)
+    st = gpu()
+    s = oracle.sizes(p)
+    v0 = si.developed_channel_velocity(p, 7).reshape(-1)
+    U0 = np.concatenate([v0, v0, np.zeros(2 * s["Mp"])])
+    Uref, info = kr.newton(p, oracle.MODN, U0, v0, vcycle_levels=3, omega=0.5, surrogate=False,
+                           coarse_solve="direct", smoother="colour", patches="vertex", tol_abs=1e-30)
+    assert info["status"] == "ok"
+    for prec in (st.ST_FP64, st.ST_FP32):
+        prob = st.Problem(p)
+        U = dev(U0)
+        status, gi = prob.newton_step(st.ST_MODN, U, dev(v0), vcycle_prec=prec, raise_on_fail=False)
+        assert status == st.ST_OK, (prec, gi)
+        Ug = U.cpu().numpy()
+        assert np.abs(Ug - Uref).max() <= 1e-6 * np.abs(Uref).max(), (prec, np.abs(Ug - Uref).max())
+        prob.close()
