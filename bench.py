@@ -194,12 +194,12 @@ CONFIG3_WORKLOAD = ("3D unit cube 64^3 hexes, Q2/Q1, dG(2) 3 Radau points, dt=0.
 
 
 def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300, smoother=0, omega=None, arms=("mixed", "fp64"),
-                  dt=None, finest=0):
+                  dt=None, finest=0, patch_type=0):
     """The 64^3, dG(2) linear solve with the FP32 V-cycle (mixed) and the FP64
     V-cycle: seconds of the preconditioner set-up and of the FGMRES solve,
     iterations and final relative residual per arm."""
     p = si.config(3, nx=mesh, ny=mesh, nz=mesh, levels=levels, coarse_solve=coarse, smoother=smoother,
-                  finest_patches=finest)
+                  finest_patches=1 if patch_type == 1 else finest, patch_type=patch_type)
     if omega is not None:
         p["omega"] = omega
     if dt is not None:
@@ -207,7 +207,8 @@ def config3_solve(st, torch, mesh=64, levels=4, coarse=0, maxit=300, smoother=0,
     s = si.sizes(p)
     K1 = p["k"] + 1
     res = {"workload": CONFIG3_WORKLOAD.replace("64^3", "%d^3" % mesh), "levels": levels,
-           "coarse_solve": coarse, "smoother": smoother, "finest_patches": finest, "omega": p["omega"], "dt": p["dt"],
+           "coarse_solve": coarse, "smoother": smoother, "finest_patches": p["finest_patches"],
+           "patch_type": patch_type, "omega": p["omega"], "dt": p["dt"],
            "dofs": s["Nst"]}
     for arm, prec in (("mixed", st.ST_FP32), ("fp64", st.ST_FP64)):
         if arm not in arms:
@@ -683,6 +684,8 @@ def main():
     ap.add_argument("--config3-arms", default="mixed,fp64")
     ap.add_argument("--config3-finest", type=int, default=0, choices=[0, 1],
                     help="finest-level patches: 0 surrogate, 1 exact")
+    ap.add_argument("--config3-patch-type", type=int, default=0, choices=[0, 1],
+                    help="Vanka patches: 0 cell, 1 vertex-star (exact)")
     args = ap.parse_args()
 
     p, U, dU, vp = si.workload(2)
@@ -713,7 +716,7 @@ def main():
         print(json.dumps(config3_solve(st, torch, args.config3_mesh, args.config3_levels, args.config3_coarse,
                                        smoother=args.config3_smoother, omega=args.config3_omega,
                                        arms=tuple(args.config3_arms.split(",")), dt=args.config3_dt,
-                                       finest=args.config3_finest)))
+                                       finest=args.config3_finest, patch_type=args.config3_patch_type)))
         return
     if args.batched_only:
         res = batched_comparison(st, torch, smoother=args.batched_smoother, omega=args.batched_omega)
