@@ -32,6 +32,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "st_internal.h"
 
 namespace st {
@@ -360,7 +362,9 @@ struct OpCfg {
   static constexpr int SP = D::NP;
   static constexpr int SQ = D::NQ;
   static constexpr int per_slot = SX + SG + SP + SQ;
-  static constexpr size_t smem_bytes = (size_t)S * per_slot * sizeof(T) + (size_t)S * sizeof(int) + 64;
+  // + per item: linear cell id, Q2 and Q1 grid index of the cell's first node, colour class
+  static constexpr size_t smem_bytes =
+      (size_t)S * per_slot * sizeof(T) + (size_t)S * sizeof(int) + 8 + (size_t)S * (2 * sizeof(long) + sizeof(int)) + 64;
 };
 
 // One batch of the volume kernel: nc items (cells in colour order; element-
@@ -379,6 +383,11 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
   T* sP = sG + S * Cfg::SG;
   T* sQ = sP + S * Cfg::SP;
   int* sCell = reinterpret_cast<int*>(sQ + S * Cfg::SQ);  // linear cell id of batch cell
+  // the cell's first Q2 and Q1 node (grid index) and its colour class, so that
+  // the per-element gathers and stores need no division by the mesh extents
+  long* sB2 = reinterpret_cast<long*>((reinterpret_cast<uintptr_t>(sCell + S) + 7) & ~(uintptr_t)7);
+  long* sB1 = sB2 + S;
+  int* sCl = reinterpret_cast<int*>(sB1 + S);
   const T* in = reinterpret_cast<const T*>(a.in);
   constexpr int SK = (MODE == OP_ELM) ? 1 : K1;  // slots per batch item
   const int ns = nc * SK;
@@ -386,8 +395,13 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
 
   // ---- batch setup: cell ids (element-matrix mode: item = (cell, column))
   for (int ci = threadIdx.x; ci < nc; ci += blockDim.x) {
+    int ex, ey, ez;
     if constexpr (MODE == OP_ELM) {
-      sCell[ci] = (int)((b0 + ci) / D::NE);
+      const int cell = (int)((b0 + ci) / D::NE);
+      sCell[ci] = cell;
+      ex = cell % a.n[0];
+      ey = (cell / a.n[0]) % a.n[1];
+      ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
     } else {
       // colour-ordered cell index -> colour class c -> cell (o + 2 i, ...)
       long li = b0 + ci;
@@ -399,9 +413,14 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
       const int i = (int)(li % cn0);
       const int j = (int)((li / cn0) % cn1);
       const int l = (int)(li / ((long)cn0 * cn1));
-      const int ex = (c & 1) + 2 * i, ey = ((c >> 1) & 1) + 2 * j, ez = (DIM == 3) ? ((c >> 2) & 1) + 2 * l : 0;
+      ex = (c & 1) + 2 * i;
+      ey = ((c >> 1) & 1) + 2 * j;
+      ez = (DIM == 3) ? ((c >> 2) & 1) + 2 * l : 0;
       sCell[ci] = ex + a.n[0] * (ey + a.n[1] * ez);
     }
+    sB2[ci] = 2L * ex + a.g2[0] * (2L * ey + a.g2[1] * 2L * ez);
+    sB1[ci] = (long)ex + a.g1[0] * ((long)ey + a.g1[1] * ez);
+    sCl[ci] = colour_of<DIM>(ex, ey, ez);
   }
   __syncthreads();
 
@@ -420,13 +439,12 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
     }
     const int ci = s / K1, mu = s % K1;
     const int cell = sCell[ci];
-    const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
     const T* src;
     T* dst;
     if (r < NC * NQ) {
       const int c = r / NQ, q = r % NQ;
       const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-      const long g = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz));
+      const long g = sB2[ci] + qx + a.g2[0] * (qy + a.g2[1] * qz);
       src = in + (long)mu * a.Mv + c * a.Nq2 + g;
       dst = sX + s * Cfg::SX + r;
     } else {
@@ -442,7 +460,7 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
         continue;
       }
       const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
-      const long g = (ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz));
+      const long g = sB1[ci] + mx + a.g1[0] * (my + a.g1[1] * mz);
       src = in + (long)K1 * a.Mv + (long)mu * a.Mp + g;
     }
     cp_async_elem<T>(dst, src);
@@ -655,7 +673,6 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
         rpass_sym<DIM, 1>(acc, ct.BtS);
         if constexpr (DIM == 3) rpass_sym<DIM, 2>(acc, ct.BtS);
         const int cell = sCell[ci];
-        const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
         if constexpr (MODE == OP_RES) {
           // value terms in nodal form: M_e (-sum_j K_ij u_j + m_i v^- + tau w_i f_i)
           const T* vp = reinterpret_cast<const T*>(a.vprev);
@@ -664,7 +681,7 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
-            const long gn = (2L * ex + qx) + a.g2[0] * ((2L * ey + qy) + a.g2[1] * (2L * ez + qz)) + c * a.Nq2;
+            const long gn = sB2[ci] + qx + a.g2[0] * (qy + a.g2[1] * qz) + c * a.Nq2;
             T t = vp ? (T)a.mt[mu] * vp[gn] : (T)0;
 #pragma unroll
             for (int j = 0; j < K1; ++j) t -= (T)a.Kt[mu * K1 + j] * in[(long)j * a.Mv + gn];
@@ -688,8 +705,7 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
         // plain stores into the private buffer of the cell's colour class:
         // cells of one class share no node, so no two threads write the same
         // entry; st_cbuf_sum adds the classes' buffers afterwards
-        T* ob = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)mu * a.Mv +
-                c * a.Nq2 + (2L * ex) + a.g2[0] * ((2L * ey) + a.g2[1] * (2L * ez));
+        T* ob = reinterpret_cast<T*>(a.cbuf) + (long)sCl[ci] * a.cbuf_stride + (long)mu * a.Mv + c * a.Nq2 + sB2[ci];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           const int qx = q % 3, qy = (q / 3) % 3, qz = (DIM == 3) ? q / 9 : 0;
@@ -704,7 +720,6 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
         for (int q = 0; q < NQ; ++q) fq[q] = sQ[s * NQ + q];
         gauss_to_q1<DIM>(fq, ct.B1, pt);
         const int cell = sCell[ci];
-        const int ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
         if constexpr (MODE == OP_ELM) {
           const long item = b0 + s;
           T* E = reinterpret_cast<T*>(a.out) + ((long)cell * a.elm_stride + a.elm_slot) * D::NE * D::NE + item % D::NE;
@@ -712,8 +727,7 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
           for (int m = 0; m < NP; ++m) E[(long)(NC * NQ + m) * D::NE] = pt[m];
           continue;
         }
-        T* pb = reinterpret_cast<T*>(a.cbuf) + (long)colour_of<DIM>(ex, ey, ez) * a.cbuf_stride + (long)K1 * a.Mv +
-                (long)mu * a.Mp;
+        T* pb = reinterpret_cast<T*>(a.cbuf) + (long)sCl[ci] * a.cbuf_stride + (long)K1 * a.Mv + (long)mu * a.Mp;
         if (a.pdisc) {
           // P1disc tests: T^T times the vertex tests, at the cell's own coefficients
 #pragma unroll
@@ -728,7 +742,7 @@ __device__ __forceinline__ void op_batch(const OpArgs& a, const long b0, const i
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
           const int mx = m & 1, my = (m >> 1) & 1, mz = (DIM == 3) ? (m >> 2) : 0;
-          pb[(ex + mx) + a.g1[0] * ((ey + my) + a.g1[1] * (ez + mz))] = pt[m];
+          pb[sB1[ci] + mx + a.g1[0] * (my + a.g1[1] * mz)] = pt[m];
         }
       }
     }
