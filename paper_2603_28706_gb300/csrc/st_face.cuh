@@ -34,7 +34,9 @@ struct FaceCfg {
   static constexpr int oFQ = oPT + D::NC * (DIM - 1) * D::NFQ;
   static constexpr int oFP = oFQ + D::NFQ;
   static constexpr int per_slot = oFP + D::NFP;
-  static constexpr size_t smem_bytes = (size_t)FS * per_slot * sizeof(T) + (size_t)FS * 4 * sizeof(int) + 64;
+  // + per slot: cell, side, face, node; the cell's first Q2 and Q1 grid index
+  static constexpr size_t smem_bytes =
+      (size_t)FS * per_slot * sizeof(T) + (size_t)FS * 4 * sizeof(int) + 8 + (size_t)FS * 2 * sizeof(long) + 64;
 };
 
 // Pointwise face terms at face point fq of one face slot whose normal is
@@ -280,6 +282,8 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
   int* sSide = sCellL + FS;
   int* sFid = sSide + FS;
   int* sMu = sFid + FS;
+  long* sB2 = reinterpret_cast<long*>((reinterpret_cast<uintptr_t>(sMu + FS) + 7) & ~(uintptr_t)7);
+  long* sB1 = sB2 + FS;
   __shared__ T sDd[3][9], sDdt[3][9];
 
   const T* in = reinterpret_cast<const T*>(a.in);
@@ -296,8 +300,12 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
       const int face = (int)(slot / K1);
       sFid[f] = face;
       sMu[f] = (int)(slot % K1);
-      sCellL[f] = face_cell[face];
+      const int cell = face_cell[face];
+      sCellL[f] = cell;
       sSide[f] = face_side[face];
+      const long ex = cell % a.n[0], ey = (cell / a.n[0]) % a.n[1], ez = (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0;
+      sB2[f] = 2 * ex + a.g2[0] * (2 * ey + a.g2[1] * 2 * ez);
+      sB1[f] = ex + a.g1[0] * (ey + a.g1[1] * ez);
     }
     __syncthreads();
 
@@ -306,7 +314,6 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
       const int f = it / (NC * NFQ + NFP), r = it % (NC * NFQ + NFP);
       const int side = sSide[f], ax = side >> 1, up = side & 1, mu = sMu[f];
       const int cell = sCellL[f];
-      const int e3[3] = {cell % a.n[0], (cell / a.n[0]) % a.n[1], (DIM == 3) ? cell / (a.n[0] * a.n[1]) : 0};
       const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
       T* w = sW + f * PS;
       if (r < NC * NFQ) {
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
           const int px = ax == 0 ? i : (t1 == 0 ? p1 : 0);
           const int py = ax == 1 ? i : (t1 == 1 ? p1 : (t2 == 1 ? p2 : 0));
           const int pz = ax == 2 ? i : (t2 == 2 ? p2 : 0);
-          const long gn = (2L * e3[0] + px) + a.g2[0] * ((2L * e3[1] + py) + a.g2[1] * (2L * e3[2] + pz));
+          const long gn = sB2[f] + px + a.g2[0] * (py + a.g2[1] * pz);
           v[i] = in[(long)mu * a.Mv + c * a.Nq2 + gn];
         }
         w[Cfg::oPV + c * NFQ + tn] = up ? v[2] : v[0];
@@ -339,7 +346,7 @@ __global__ void __launch_bounds__(OP_THREADS) st_face_kernel(const OpArgs a, con
           for (int j = 1; j <= DIM; ++j) v += ((mc >> (j - 1)) & 1) ? pc[j] : -pc[j];
           w[Cfg::oFP + m] = v;
         } else {
-          const long gp = (e3[0] + mx) + a.g1[0] * ((e3[1] + my) + a.g1[1] * (e3[2] + mz));
+          const long gp = sB1[f] + mx + a.g1[0] * (my + a.g1[1] * mz);
           w[Cfg::oFP + m] = in[(long)K1 * a.Mv + (long)mu * a.Mp + gp];
         }
       }
