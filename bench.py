@@ -346,7 +346,7 @@ def batched_comparison(st, torch, step=True, smoother=0, omega=None):
 
 
 SWEEP_WORKLOAD = ("2D channel 4x1, 4n x n cells (n in SWEEP_MESHES), Q2/Q1, dG(1), dt=1, parabolic Nitsche inflow "
-                  "vbar=0.1 at x=0, no-slip walls, do-nothing outflow, nu=1e-3, nu_inf=0, sigma_max=1e-4; initial "
+                  "vbar=0.1 at x=0, no-slip walls, do-nothing outflow, nu=1e-3, nu_inf=0, sigma_max as given; initial "
                   "velocity: the "
                   "parabolic inflow profile plus 0.1 x an 8-mode Fourier field (seed 7); SWEEP_SLABS slabs, each "
                   "slab's Newton step started from the previous solution, |R|_M <= 1e-8 |R0|_M, at most 30 "
@@ -412,7 +412,8 @@ def sweep_instance(st, torch, p, tangent, slabs, vprec):
             "W": work(n_l, n) if ok else None, "n_nl_mean": float(np.mean(n_nl)) if ok else None}
 
 
-def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=None, smoother="additive"):
+def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=None, smoother="additive",
+                     sigma_max=1e-4):
     """Analogue of the solver evaluation of Sec. 7 (Table newton-compact, eq.
     work, eq. perf-profile) on synthetic channel problems: every (p, delta,
     mesh) instance with Pic, exN and modN.  patches: "surrogate" or "exact"
@@ -427,7 +428,7 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=No
         for delta in SWEEP_DELTA:
             for pe in SWEEP_P:
                 prm = si.base_params(dim=2, nx=4 * n, ny=n, Lx=4.0, Ly=1.0, k=1, dt=1.0, p=pe, delta=delta,
-                                     nu=1e-3, nu_inf=0.0, sigma_max=1e-4, inflow_profile=1, vbar=0.1,
+                                     nu=1e-3, nu_inf=0.0, sigma_max=sigma_max, inflow_profile=1, vbar=0.1,
                                      levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30,
                                      finest_patches=0 if patches == "surrogate" else 1,
                                      smoother=0 if smoother == "additive" else 1,
@@ -442,6 +443,7 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=No
     taus = [1.0, 1.25, 1.5, 2.0, 3.0, 5.0, 10.0]
     prof = perf_profile(W, taus)
     return {"workload": SWEEP_WORKLOAD, "vcycle": vprec_name, "finest_patches": patches, "smoother": smoother,
+            "sigma_max": sigma_max,
             "omega": omega if omega is not None else si.base_params(dim=2)["omega"],
             "meshes_cells": [4 * n * n for n in SWEEP_MESHES],
             "p": list(SWEEP_P),
@@ -661,6 +663,7 @@ def main():
     ap.add_argument("--sweep-omega", type=float, default=None, help="Vanka damping of the sweep (default: 2D default)")
     ap.add_argument("--sweep-smoother", default="additive", choices=["additive", "colour"],
                     help="Vanka step of the sweep: additive (eq. stmg-vanka-update) or colour-multiplicative")
+    ap.add_argument("--sweep-sigma-max", type=float, default=1e-4, help="modN stress clip of the sweep")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--newton-levels", type=int, default=5, help="V-cycle levels of the Newton comparison")
@@ -725,7 +728,7 @@ def main():
         return
     if args.sweep:
         print(json.dumps(robustness_sweep(st, torch, args.sweep_vcycle, args.sweep_patches, args.sweep_omega,
-                                          args.sweep_smoother)))
+                                          args.sweep_smoother, args.sweep_sigma_max)))
         return
     stream = torch.cuda.current_stream()
     if args.cip_only:
