@@ -77,3 +77,31 @@ def test_binding_carries_the_optional_fields():
     # the allocation-free mass norm implements the Q2/Q1 pair only
     with pytest.raises(ValueError):
         st.mnorm_noalloc(si.base_params(pressure_space=1), None)
+
+
+def test_binding_struct_layout_matches_the_header(tmp_path):
+    # the ctypes mirrors of the parameter and info structs against the C
+    # compiler's layout of include/st.h (size and every field offset)
+    import shutil
+    import subprocess
+    import paper_2603_28706_gb300 as st
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"st_params": st.StParams, "st_linsolve_info": st.StLinsolveInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "st.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
