@@ -102,10 +102,11 @@ NEWTON_GEOMETRY = ("3D channel 4x1x1, 128x32x32 hexes, Q2/Q1, dG(1) 2 Radau poin
 NEWTON_CASES = (
     # (name, p, delta, start, solver overrides): the stated parameters from the Dirichlet lifting, and a
     # milder (p, delta) from rest at which every arm converges (the timing comparison), with the additive
-    # Vanka step and with the colour-multiplicative one
+    # Vanka step, the colour-multiplicative one, and the latter on the finest level only
     ("stated", 1.1, 1e-6, "lifting", {}),
     ("p1.5_delta1e-3", 1.5, 1e-3, "rest", {}),
     ("p1.5_delta1e-3_colour", 1.5, 1e-3, "rest", {"smoother": 1, "omega": 0.5}),
+    ("p1.5_delta1e-3_colour_finest", 1.5, 1e-3, "rest", {"smoother": 2, "omega": 0.5, "omega_coarse": 0.1}),
 )
 
 

@@ -113,7 +113,9 @@ typedef struct {
                                  parities px + 2 py + 4 pz, in that order), a fresh
                                  defect before each class: multiplicative between
                                  classes, additive inside one (its cells share no
-                                 dof); 2^dim defects per step                        */
+                                 dof); 2^dim defects per step; 2: the class-by-class
+                                 step on the finest level, the additive step with
+                                 omega_coarse on the coarser levels                  */
   int patch_type;             /* Vanka patches (Sec. 6.3): 0 = cell patches (every dof
                                  of a cell); 1 = vertex-star patches: the velocity
                                  nodes of the 2^dim cells around a vertex that are not
@@ -121,6 +123,8 @@ typedef struct {
                                  pressure, all k+1 time nodes, classes by vertex
                                  parity; exact patches only (finest_patches = 1,
                                  gamma_cip = 0, pressure_space = 0)                  */
+  double omega_coarse;        /* Vanka damping below the finest level with smoother = 2
+                                 (0 = omega)                                          */
 } st_params;
 
 typedef struct {

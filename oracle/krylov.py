@@ -82,7 +82,7 @@ def fgmres(apply_A, b, precond, M, rtol, restart=50, maxit=200, atol=0.0):
 def newton(p, var, U0, vprev, f=None, vcycle_levels=1, max_iter=30, tol_abs=1e-12, tol_rel=1e-8, omega=0.2,
            pre=2, post=2, coarse_sweeps=8, restart=50, maxit=200, lin_rtol=1e-8, ew_gamma=0.9, ew_alpha=2.0,
            ew_max=0.1, armijo_c=1e-4, lambda_min=1.0 / 64, rho=0.5, surrogate=True, coarse_solve="sweeps",
-           smoother="additive", patches="cell"):
+           smoother="additive", patches="cell", omega_coarse=None):
     """Slab Newton solve; returns (U, info dict with per-iteration history)."""
     M = mass_matrix(p)
     mnorm = lambda r: float(np.sqrt(r @ (M @ r)))
@@ -105,7 +105,8 @@ def newton(p, var, U0, vprev, f=None, vcycle_levels=1, max_iter=30, tol_abs=1e-1
             (len(lin_its) >= 2 and lin_its[-1] > 2 * lin_its[-2])
         if H is None:
             H = mg.Hierarchy(p, var, U, vcycle_levels, omega, pre, post, coarse_sweeps, surrogate=surrogate,
-                                 coarse_solve=coarse_solve, smoother=smoother, patches=patches)
+                                 coarse_solve=coarse_solve, smoother=smoother, patches=patches,
+                                 omega_coarse=omega_coarse)
         else:
             H.update(var, U, rebuild_finest=rebuild)
         rebuilds += int(rebuild)

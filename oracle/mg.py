@@ -28,7 +28,9 @@ restatement on the oracle's assembled matrices, small meshes only:
                      of cells (cell parities (px, py, pz), class px + 2 py +
                      4 pz, in that order), a fresh defect before each class:
                      multiplicative Schwarz between classes, additive within
-                     one (cells of a class share no dof)
+                     one (cells of a class share no dof); smoother=
+                     "colour_finest": that on the finest level, the additive
+                     step with omega_coarse below it
   vcycle             pre-smoothing, restriction, recursion, coarsest-level
                      treatment, prolongation, post-smoothing
 Readings (the paper defers to its references here): the coarsest level is
@@ -229,11 +231,11 @@ class Hierarchy:
     (the refresh rule of Sec. 6.3 keeps them otherwise)."""
 
     def __init__(self, p, var, U, levels, omega, pre, post, coarse_sweeps=8, surrogate=True,
-                 coarse_solve="sweeps", smoother="additive", patches="cell"):
+                 coarse_solve="sweeps", smoother="additive", patches="cell", omega_coarse=None):
         if coarse_solve not in ("sweeps", "direct"):
             raise ValueError("coarse_solve must be 'sweeps' or 'direct'")
-        if smoother not in ("additive", "colour"):
-            raise ValueError("smoother must be 'additive' or 'colour'")
+        if smoother not in ("additive", "colour", "colour_finest"):
+            raise ValueError("smoother must be 'additive', 'colour' or 'colour_finest'")
         if patches not in ("cell", "vertex"):
             raise ValueError("patches must be 'cell' or 'vertex'")
         if patches == "vertex" and surrogate:
@@ -243,6 +245,7 @@ class Hierarchy:
         self.p, self.levels = p, levels
         self.smoother = smoother
         self.patches = patches
+        self.omega_coarse = omega if not omega_coarse else omega_coarse
         self.coarse_solve = coarse_solve
         self.lu0 = None
         self.omega = omega
@@ -284,14 +287,16 @@ class Hierarchy:
 
     def vanka_step(self, l, r, d):
         A = self.op(l)
-        if self.smoother == "colour":
+        finest = l == self.levels - 1
+        if self.smoother == "colour" or (self.smoother == "colour_finest" and finest):
             cls = vertex_classes(self.params[l]) if self.patches == "vertex" else colour_classes(self.params[l])
             return colour_sweep(A, self.Ainv[l], self.dofs[l], cls, self.omega, r, d)
+        omega = self.omega_coarse if self.smoother == "colour_finest" else self.omega
         defect = r - A @ d
         corr = np.zeros_like(d)
         for c, dof in enumerate(self.dofs[l]):
             corr[dof] += self.Ainv[l][c] @ defect[dof]
-        return d + self.omega * corr
+        return d + omega * corr
 
     def smooth(self, l, r, d, sweeps):
         for _ in range(sweeps):

@@ -42,7 +42,7 @@ class StParams(ctypes.Structure):
                 ("armijo_c", ctypes.c_double), ("lambda_min", ctypes.c_double),
                 ("coarse_sweeps", ctypes.c_int), ("gamma_cip", ctypes.c_double), ("finest_patches", ctypes.c_int),
                 ("coarse_solve", ctypes.c_int), ("pressure_space", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("patch_type", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("patch_type", ctypes.c_int), ("omega_coarse", ctypes.c_double)]
 
 
 class StNewtonInfo(ctypes.Structure):
@@ -127,7 +127,7 @@ def load(build_if_missing=True):
 
 
 _OPTIONAL = {"gamma_cip": 0.0, "finest_patches": 0, "coarse_solve": 0, "pressure_space": 0, "smoother": 0,
-             "patch_type": 0}
+             "patch_type": 0, "omega_coarse": 0.0}
 
 
 def params(p):

@@ -244,7 +244,9 @@ st_status check_params(const st_params& P, std::string& why) {
   if (P.inflow_profile != 0 && P.inflow_profile != 1) return why = "inflow_profile must be 0 or 1", ST_EINVAL;
   if (P.coarse_solve != 0 && P.coarse_solve != 1) return why = "coarse_solve must be 0 or 1", ST_EINVAL;
   if (P.pressure_space != 0 && P.pressure_space != 1) return why = "pressure_space must be 0 or 1", ST_EINVAL;
-  if (P.smoother != 0 && P.smoother != 1) return why = "smoother must be 0 or 1", ST_EINVAL;
+  if (P.smoother < 0 || P.smoother > 2) return why = "smoother must be 0, 1 or 2", ST_EINVAL;
+  if (!(P.omega_coarse >= 0.0) || !std::isfinite(P.omega_coarse))
+    return why = "omega_coarse must be finite and >= 0", ST_EINVAL;
   if (P.patch_type != 0 && P.patch_type != 1) return why = "patch_type must be 0 or 1", ST_EINVAL;
   if (P.patch_type == 1 && (P.finest_patches != 1 || P.gamma_cip > 0 || P.pressure_space != 0))
     return why = "patch_type = 1 (vertex-star patches) needs finest_patches = 1, gamma_cip = 0 and pressure_space = 0",

@@ -1769,7 +1769,8 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
   // smoother 0: one pass over all cells into the class buffers, then
   // d += omega sum of the buffers; smoother 1: one pass per colour class,
   // each after a fresh defect, adding omega x into d directly
-  const bool mult = h->P.smoother == 1;
+  const bool finest = l == (int)h->lev.size() - 1;
+  const bool mult = h->P.smoother == 1 || (h->P.smoother == 2 && finest);
   const int npass = mult ? cm.nclass : 1;
   // vertex-star patches (patch_type = 1): their own classes and buffers
   const bool vtx = h->P.patch_type == 1;
@@ -1780,7 +1781,7 @@ cudaError_t vanka_steps(st_problem* h, MgState* m, int l, int sweeps, const T* r
   const int nt0 = Np <= 128 ? 128 : 256;
   const LaunchShape cand[5] = {{nt0, 16L * h->nsm}, {128, 16L * h->nsm}, {256, 8L * h->nsm}, {512, 4L * h->nsm},
                                {128, 32L * h->nsm}};
-  const T om = (T)h->P.omega;
+  const T om = (T)(h->P.smoother == 2 && !finest && h->P.omega_coarse > 0 ? h->P.omega_coarse : h->P.omega);
   for (int s = 0; s < sweeps; ++s) {
     for (int c = 0; c < npass; ++c) {
       const long li0 = mult ? pm.start[c] : 0, nli = mult ? pm.start[c + 1] - pm.start[c] : npatch;

@@ -31,7 +31,7 @@ def base_params(**kw):
              levels=1, pre_smooth=2, post_smooth=2, omega=0.25, rho_refresh=0.5,
              fgmres_restart=50, fgmres_maxit=200, newton_maxit=30, tol_abs=1e-12, tol_rel=1e-8,
              lin_rtol=1e-8, ew_gamma=0.9, ew_alpha=2.0, ew_max=0.1, armijo_c=1e-4, lambda_min=1.0 / 64,
-             coarse_sweeps=8, finest_patches=0, coarse_solve=0, smoother=0, patch_type=0)
+             coarse_sweeps=8, finest_patches=0, coarse_solve=0, smoother=0, patch_type=0, omega_coarse=0.0)
     p.update(kw)
     if p["dim"] == 2:
         p["nz"] = 1

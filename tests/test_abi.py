@@ -43,7 +43,7 @@ def test_setup_rejects_bad_parameters_without_gpu():
     for bad in (dict(dim=4), dict(p=2.5), dict(k=7), dict(levels=3, nx=6), dict(delta=0.0), dict(nx=0),
                 dict(gamma_cip=-1.0), dict(finest_patches=2), dict(finest_patches=1, gamma_cip=1.0),
                 dict(coarse_solve=2), dict(coarse_solve=1, nx=16, ny=16, nz=16, levels=1), dict(pressure_space=2),
-                dict(smoother=2), dict(patch_type=2),
+                dict(smoother=3), dict(omega_coarse=-1.0), dict(patch_type=2),
                 dict(patch_type=1, finest_patches=0), dict(patch_type=1, finest_patches=1, gamma_cip=0.5),
                 dict(patch_type=1, finest_patches=1, pressure_space=1)):
         P = st.params(si.base_params(**bad))

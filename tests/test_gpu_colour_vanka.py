@@ -122,3 +122,25 @@ def test_colour_newton_matches_oracle():
         R0 = oracle.residual(p, U0, vprev=v0)
         assert np.sqrt(oracle.mnorm2(p, R)) <= 1e-8 * np.sqrt(oracle.mnorm2(p, R0)) * 1.01
         prob.close()
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nx=8, ny=4, k=1, levels=3, inflow_profile=1),
+                                  dict(dim=3, nx=4, ny=4, nz=4, k=1, levels=2)])
+def test_colour_finest_vcycle(case):
+    # smoother = 2: the colour step on the finest level, the additive step
+    # with omega_coarse below it
+    p = si.base_params(p=1.4, delta=0.1, nu=0.1, nu_inf=0.01, sigma_max=0.05, coarse_sweeps=3, smoother=2,
+                       omega=0.5, omega_coarse=0.15, **case)
+    st = gpu()
+    U = si.fourier_state(p, 0)
+    r = si.uniform(oracle.sizes(p)["Nst"], 1)
+    H = mg.Hierarchy(p, VAR[2], U, p["levels"], 0.5, p["pre_smooth"], p["post_smooth"],
+                     coarse_sweeps=p["coarse_sweeps"], surrogate=True, smoother="colour_finest", omega_coarse=0.15)
+    ref = H.vcycle(r)
+    prob = st.Problem(p)
+    prob.linearize(2, dev(U))
+    for prec, dt, tol in ((st.ST_FP64, torch.float64, TOL64), (st.ST_FP32, torch.float32, TOL32)):
+        for _ in range(2):
+            d = prob.vcycle(dev(r, dt), prec=prec)
+            assert rel(d, ref) <= tol, (prec, rel(d, ref))
+    prob.close()

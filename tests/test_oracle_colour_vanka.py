@@ -105,3 +105,19 @@ def test_smoother_name_is_checked():
     p = si.base_params(dim=2, nx=2, ny=2, k=1)
     with pytest.raises(ValueError):
         mg.Hierarchy(p, oracle.PIC, si.uniform_state(p, 0), 1, 1.0, 1, 1, smoother="gauss")
+
+
+def test_colour_finest_combines_the_two_steps():
+    # smoother="colour_finest": the finest level takes the colour step with
+    # omega, the coarser levels the additive step with omega_coarse
+    p = si.base_params(dim=2, nx=4, ny=4, k=1, p=1.4, delta=0.1, nu=0.3, nu_inf=0.05, sigma_max=0.1)
+    s = oracle.sizes(p)
+    U = si.uniform_state(p, 0)
+    r = si.uniform(s["Nst"], 1)
+    Hh = mg.Hierarchy(p, oracle.MODN, U, 2, 0.6, 1, 1, surrogate=False, smoother="colour_finest", omega_coarse=0.2)
+    Hc = mg.Hierarchy(p, oracle.MODN, U, 2, 0.6, 1, 1, surrogate=False, smoother="colour")
+    Ha = mg.Hierarchy(p, oracle.MODN, U, 2, 0.2, 1, 1, surrogate=False, smoother="additive")
+    rc = si.uniform(oracle.sizes(Hh.params[0])["Nst"], 2)
+    z = np.zeros_like(r)
+    np.testing.assert_array_equal(Hh.vanka_step(1, r, z), Hc.vanka_step(1, r, z))
+    np.testing.assert_array_equal(Hh.vanka_step(0, rc, np.zeros_like(rc)), Ha.vanka_step(0, rc, np.zeros_like(rc)))
