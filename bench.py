@@ -432,7 +432,8 @@ def robustness_sweep(st, torch, vprec_name="fp32", patches="surrogate", omega=No
                                      nu=1e-3, nu_inf=0.0, sigma_max=sigma_max, inflow_profile=1, vbar=0.1,
                                      levels=levels, tol_rel=1e-8, tol_abs=1e-30, coarse_sweeps=8, newton_maxit=30,
                                      finest_patches=0 if patches == "surrogate" else 1,
-                                     smoother=0 if smoother == "additive" else 1,
+                                     smoother={"additive": 0, "colour": 1, "colour_finest": 2}[smoother],
+                                     omega_coarse=0.2 if smoother == "colour_finest" else 0.0,
                                      patch_type=1 if patches == "vertex" else 0)
                 if omega is not None:
                     prm["omega"] = omega
@@ -662,8 +663,9 @@ def main():
                     help="Vanka patches of the sweep: cell patches with the surrogate of eq. surrogate-diag or "
                          "exact on the finest level, or exact vertex-star patches")
     ap.add_argument("--sweep-omega", type=float, default=None, help="Vanka damping of the sweep (default: 2D default)")
-    ap.add_argument("--sweep-smoother", default="additive", choices=["additive", "colour"],
-                    help="Vanka step of the sweep: additive (eq. stmg-vanka-update) or colour-multiplicative")
+    ap.add_argument("--sweep-smoother", default="additive", choices=["additive", "colour", "colour_finest"],
+                    help="Vanka step of the sweep: additive (eq. stmg-vanka-update), colour-multiplicative, or "
+                         "colour-multiplicative on the finest level only (additive with omega 0.2 below)")
     ap.add_argument("--sweep-sigma-max", type=float, default=1e-4, help="modN stress clip of the sweep")
     ap.add_argument("--newton-mesh", type=int, nargs=3, default=[128, 32, 32], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--newton-arms", default="mixed,fp64", help="comma list of mixed, fp64")
