@@ -45,3 +45,16 @@ def test_failure_kind_names_the_stopping_cause():
     assert bench.failure_kind(st, st.ST_LINESEARCH_FAILED, 3, 30) == "linesearch"
     assert bench.failure_kind(st, st.ST_NOT_CONVERGED, 30, 30) == "newton_cap"
     assert bench.failure_kind(st, st.ST_NOT_CONVERGED, 2, 30) == "linear"
+
+
+def test_hierarchy_for_coarsens_to_an_odd_or_two_cell_level():
+    import st_inputs as si
+    for n, levels, direct in ((8, 3, 1), (32, 5, 1), (30, 2, 0), (28, 3, 0), (12, 3, 1), (16, 4, 1)):
+        p = bench.hierarchy_for(si.base_params(dim=3, nx=n, ny=n, nz=n, k=1))
+        assert p["levels"] == levels, (n, p["levels"])
+        nc = n // 2 ** (levels - 1)
+        assert nc % 2 == 1 or nc == 2
+        n0 = 2 * (3 * (2 * nc + 1) ** 3 + (nc + 1) ** 3)
+        assert p["coarse_solve"] == direct and (n0 <= 20000) == bool(direct), (n, n0)
+    q = bench.hierarchy_for(si.base_params(dim=3, nx=8, ny=8, nz=8), smoother=2, omega=0.4)
+    assert q["smoother"] == 2 and q["omega"] == 0.4
